@@ -1,0 +1,190 @@
+/*
+ * md.h -- C ABI of the GB300 minimum-distance library.
+ *
+ * The library computes the minimum distance d of a binary linear code [n, k] and a
+ * codeword of weight d, with the Brouwer-Zimmermann algorithm as described in Section 2.1
+ * (Alg. 1) of Quintana-Orti, Hernando and Igual, "Parallel implementations for computing
+ * the minimum distance of a random linear code on multicomputers":
+ *
+ *   - disjoint information sets S_1..S_m of G and the systematic matrices
+ *     Gamma_j = (I_k | A_j), plus Gamma_m = [[I_{k_m}, A], [0, B]] for the leftover columns
+ *     (Section 2.1), are built on the host by elimination over F2;
+ *   - for g = 1, 2, ... and each Gamma_j, every sum of g rows of Gamma_j is formed on the
+ *     GPU and its weight tightens the upper bound U (Alg. 1, the U update);
+ *   - after each Gamma matrix the bounds are compared (Section 2.2) and after each stage
+ *     the lower bound becomes L(g) = sum_j max(0, g + 1 - (k - k_j)) (Alg. 1, the L
+ *     update); the run stops once L >= U and returns d = U.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are bit-packed rows of uint64 words: row i of a k x n matrix occupies
+ *     words [i * ceil(n/64), (i + 1) * ceil(n/64)); bit t of word w is column 64w + t.
+ *     Bits beyond column n - 1 must be zero.
+ *   - Every call returns an int status (MD_OK or an MD_E* code) and never aborts the
+ *     process.  Output arguments are written only when the call returns MD_OK.
+ *   - Input buffers are host memory, read during the call and not retained (the library
+ *     copies what it needs).  Output buffers are caller-owned host memory.
+ *   - A handle may be used by one thread at a time; distinct handles are independent.
+ *   - The witness is canonical: among all codewords of weight d that the run enumerates,
+ *     the first in (stage g, matrix j, colexicographic rank of the row combination) order.
+ *     The colex rank of rows c_1 < ... < c_g (0-based) is sum_i C(c_i, i).
+ */
+#ifndef MD_H
+#define MD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+enum {
+    MD_OK = 0,
+    MD_EINVAL = 1,        /* bad argument: n < 1, k < 1, k > n, NULL pointer, padding bits set */
+    MD_ERANK = 2,         /* G is not of full row rank k */
+    MD_EUNSUPPORTED = 3,  /* n > MD_MAX_N, or a level with C(k, g) >= 2^55 combinations */
+    MD_ENOMEM = 4,        /* host or device allocation failed */
+    MD_ECUDA = 5,         /* a CUDA runtime call failed, or no usable GPU */
+    MD_EBUDGET = 6,       /* the work would exceed md_options.work_budget combinations */
+    MD_ECANCELED = 7,     /* the run was cancelled through md_options.cancel_flag */
+    MD_ETIMEOUT = 8,      /* a bounded device-side wait gave up */
+    MD_EBUSY = 9,         /* server: the request is still pending */
+    MD_EINTERNAL = 10     /* an internal consistency check failed */
+};
+
+#define MD_MAX_N 256      /* longest code supported */
+#define MD_MAX_GAMMA 256  /* at most n information sets */
+#define MD_MAX_LEVELS 1024
+
+/* Opaque handle of one code: built by md_create, released by md_destroy. */
+typedef struct md_ctx *md_handle;
+
+/* Options.  Zero-initialise, or call md_options_init, then set fields. */
+typedef struct md_options {
+    uint64_t work_budget;     /* max combinations to enumerate; 0 = unlimited.  Exceeding it
+                                 (estimated before a stage starts) returns MD_EBUDGET */
+    int max_stage;            /* stop after this stage g even if L < U; 0 = run to the end.
+                                 The result is then the best weight found (an upper bound)
+                                 and md_info reports complete = 0 */
+    int chunk_log2;           /* log2 of the combinations per work item; 0 = default (20) */
+    int threads_per_block;    /* 0 = default (512) */
+    int blocks_per_sm;        /* 0 = default (occupancy-derived) */
+    int filter;               /* 1 (default) = reject codewords with a one-popcount lower
+                                 bound when it proves wt > U; 0 = exact weight of every
+                                 codeword; 2 = always filter */
+    void *stream;             /* cudaStream_t to run on; NULL = the library's own stream */
+    volatile int *cancel_flag;/* optional host flag (pinned or ordinary memory): set non-zero
+                                 to cancel; polled between stages */
+} md_options;
+
+/* Result details of the last md_compute on a handle. */
+typedef struct md_info {
+    int n, k;
+    int m;                         /* number of Gamma matrices */
+    int ranks[MD_MAX_GAMMA];       /* k_j of each Gamma_j (k for a full information set) */
+    int d;                         /* minimum distance (or best weight if incomplete) */
+    int complete;                  /* 1 if L >= U was reached (d exact) */
+    int lower_bound;               /* L when the run stopped */
+    int key_g, key_j;              /* canonical witness key: stage, matrix (0-based) */
+    uint64_t key_rank;             /* ... and colex rank */
+    int stop_g, stop_j;            /* last level processed */
+    int nlevels;                   /* levels processed */
+    uint64_t codewords;            /* combinations enumerated (sum of C(k, g) over levels) */
+    double seconds_total;          /* wall time of md_compute */
+    double seconds_device;         /* device time of the enumeration kernels */
+    int gpu_launches;              /* kernels launched by the last md_compute */
+} md_info;
+
+/* One processed level: stage g, matrix j, and the least weight of that level with its
+   first colex rank.  weight = -1 when the level's least weight exceeds the bound U held
+   before the level (the level cannot change U or the witness); the kernels only resolve
+   weights up to that bound. */
+typedef struct md_level {
+    int g, j;
+    int weight;
+    int pad;
+    uint64_t first_rank;
+    uint64_t count;                /* C(k, g) */
+} md_level;
+
+/* Fill *opt with defaults.  Always MD_OK (MD_EINVAL for NULL). */
+int md_options_init(md_options *opt);
+
+/* Build a handle for the code generated by the k x n matrix G (copied).
+   Validates G (MD_EINVAL, MD_EUNSUPPORTED for n > MD_MAX_N), checks full row rank
+   (MD_ERANK), finds the information sets and the Gamma_j on the host.  No device work. */
+int md_create(const uint64_t *G, int n, int k, md_handle *out);
+int md_create_ex(const uint64_t *G, int n, int k, const md_options *opt, md_handle *out);
+
+/* Run Brouwer-Zimmermann on the GPU.  *d receives the minimum distance; witness
+   (ceil(n/64) caller-owned words, may be NULL) receives the canonical codeword of weight
+   d.  Device buffers are allocated on the first call and reused. */
+int md_compute(md_handle h, int *d, uint64_t *witness);
+
+/* Details of the last md_compute (md_create alone fills n, k, m, ranks). */
+int md_info_get(md_handle h, md_info *info);
+
+/* Per-level records of the last md_compute: up to max entries, *count = levels written. */
+int md_levels(md_handle h, md_level *levels, int max, int *count);
+
+/* Gamma_j as built on the host (k x n, full rows in the original column order) and the
+   column order of its reduction (information set first); either pointer may be NULL. */
+int md_gamma(md_handle h, int j, uint64_t *gamma, int *order);
+
+/* Least weight over the colex ranks [r0, r1) of the g-row combinations of Gamma_j,
+   computed on the GPU with the enumeration kernel, and the first rank reaching it.
+   With bound >= 0 only weights <= bound are resolved (*weight = -1 if none);
+   bound < 0 resolves the exact least weight.  The whole level is r0 = 0, r1 = C(k, g). */
+int md_scan_range(md_handle h, int g, int j, uint64_t r0, uint64_t r1, int bound,
+                  int *weight, uint64_t *first_rank);
+
+void md_destroy(md_handle h);
+
+/* Static text for a status code. */
+const char *md_strerror(int code);
+
+/* ---- batched codes ------------------------------------------------------------------
+ * md_batch runs many codes of uneven n, k to completion in persistent launches: each
+ * code keeps its own U, L, stage and level records on the device, and idle warps steal
+ * work from any code.  codes[i].G follows the packing rule above.  d[i] and status[i]
+ * are written per code; witness (may be NULL) receives code i's witness at word offset
+ * sum_{t<i} ceil(n_t/64).  Returns MD_OK if the batch ran (per-code errors are in
+ * status[]), or an error for the whole call. */
+typedef struct md_code {
+    const uint64_t *G;
+    int n, k;
+} md_code;
+
+int md_batch(const md_code *codes, int count, const md_options *opt,
+             int *d, uint64_t *witness, int *status);
+
+/* ---- continuous-batching server -------------------------------------------------------
+ * A server owns a device region for resident codes and a host thread that admits
+ * submitted codes into free slots while others run, by memory and by estimated work.
+ * Results are identical to md_compute on the same code. */
+typedef struct md_server md_server;
+
+typedef struct md_server_opts {
+    int slots;                  /* codes resident on the device at once (0 = default 64) */
+    uint64_t work_budget;       /* per-request estimated combinations; larger requests are
+                                   rejected with MD_EBUDGET (0 = unlimited) */
+    size_t device_bytes;        /* device memory for resident codes (0 = default 256 MiB) */
+    void *stream;               /* cudaStream_t or NULL */
+} md_server_opts;
+
+int md_server_create(const md_server_opts *opts, md_server **out);
+/* Copies G; returns a ticket.  MD_EINVAL / MD_ERANK / MD_EUNSUPPORTED / MD_EBUDGET are
+   reported here, before the request is queued. */
+int md_server_submit(md_server *s, const uint64_t *G, int n, int k, uint64_t *ticket);
+/* MD_OK with *d, witness (ceil(n/64) words, may be NULL) and *status filled when done;
+   MD_EBUSY while pending; MD_EINVAL for an unknown ticket.  A finished ticket is
+   released by the poll that returns it. */
+int md_server_poll(md_server *s, uint64_t ticket, int *d, uint64_t *witness, int *status);
+void md_server_destroy(md_server *s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MD_H */

@@ -1,0 +1,64 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case below plants one mistake in a private copy of md_oracle.c (a dropped term, a
+wrong bound, an index off by one, a transposed comparison), builds it on the CPU, and
+runs the pin suite (tests/test_oracle_pins.py) against that build in a subprocess.  The
+suite must fail for every mutant.  The real oracle source is never modified.
+"""
+import os
+import subprocess
+import sys
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "md_oracle.c")
+
+MUTANTS = {
+    "colex_reset_off_by_one": ("for (int t = 0; t < i; t++) c[t] = t;", "for (int t = 0; t < i; t++) c[t] = t + (t > 0);"),
+    "colex_rank_position": ("r += mdo_binomial(c[i], i + 1);", "r += mdo_binomial(c[i], i);"),
+    "unrank_comparison": ("while (mdo_binomial(v, i) > rank) v--;", "while (mdo_binomial(v, i) >= rank && v > 0) v--;"),
+    "bound_drops_plus_one": ("int64_t t = (int64_t)g + 1 - (k - ranks[j]);", "int64_t t = (int64_t)g - (k - ranks[j]);"),
+    "bound_sign": ("int64_t t = (int64_t)g + 1 - (k - ranks[j]);", "int64_t t = (int64_t)g + 1 + (k - ranks[j]);"),
+    "stop_check_strict": ("if (L >= U) { stop = 1; break; }", "if (L > U) { stop = 1; break; }"),
+    "no_per_matrix_check": ("if (L >= U) { stop = 1; break; }", "(void)0;"),
+    "last_rank_not_first": ("if (w < J->minw) { J->minw = w; J->first = rank; }", "if (w <= J->minw) { J->minw = w; J->first = rank; }"),
+    "echelon_not_reduced": ("            if (t != r && get_bit(Gam + (size_t)t * nw, col)) xor_row(Gam + (size_t)t * nw, Gam + (size_t)r * nw, nw);",
+                            "            if (t > r && get_bit(Gam + (size_t)t * nw, col)) xor_row(Gam + (size_t)t * nw, Gam + (size_t)r * nw, nw);"),
+    "words_truncated": ("static int words_for(int n) { return (n + 63) / 64; }", "static int words_for(int n) { return n / 64 + (n < 64); }"),
+    "gray_code_bit": ("int b = __builtin_ctzll(i);", "int b = __builtin_ctzll(i) ^ (__builtin_ctzll(i) == 1);"),
+    "skip_last_gamma": ("        for (int j = 0; j < m; j++) {\n            int w; uint64_t first;", "        for (int j = 0; j < m - (m > 1); j++) {\n            int w; uint64_t first;"),
+    "witness_drops_row": ("for (int i = 0; i < key_g; i++) xor_row(witness", "for (int i = 1; i < key_g; i++) xor_row(witness"),
+    "info_set_not_greedy": ("for (int q = 0; q < nrem && r < k; q++) {\n            int col = remaining[q];", "for (int q = 0; q < nrem && r < k; q++) {\n            int col = remaining[nrem - 1 - q];"),
+    "partial_set_rank_off": ("            ranks[m++] = r;\n", "            ranks[m++] = r - (r > 1);\n"),
+    "weight_ignores_column0": ("for (int i = 0; i < nw; i++) w += __builtin_popcountll(row[i]);", "for (int i = 0; i < nw; i++) w += __builtin_popcountll(row[i] & (i ? ~0ull : ~1ull));"),
+}
+
+
+def _build_mutant(name, tmpdir):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation anchor for %s must occur exactly once" % name
+    path = os.path.join(tmpdir, name + ".c")
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    lib = os.path.join(tmpdir, name + ".so")
+    subprocess.run(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-pthread", path, "-o", lib], check=True)
+    return lib
+
+
+def _pins_fail(lib):
+    env = dict(os.environ, MDO_ORACLE_LIB=lib)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                       env=env, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    return r.returncode != 0, r.stdout[-2000:]
+
+
+def test_every_mutant_is_caught(tmp_path):
+    libs = {name: _build_mutant(name, str(tmp_path)) for name in MUTANTS}
+    with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
+        results = dict(zip(libs, ex.map(_pins_fail, libs.values())))
+    survivors = [name for name, (failed, _) in results.items() if not failed]
+    assert not survivors, "mutants not caught by the pins: %s" % survivors
