@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark: Brouwer-Zimmermann enumeration throughput on the random [200,100] code.
+
+One step = md_compute on G = [I_100 | R] (R from SplitMix64 seed 3, the first invertible
+draw) running every level of stages g = 1..--max-stage (default 10) to completion: both
+Gamma matrices, every g-row combination, ~3.9e13 codewords at g <= 10.  The metric is
+codewords/s = the sum of C(k, g) over the completed levels / device time.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--time-to-d]
+
+Under torchrun (N > 1) every rank runs an independent replica of the step on its own GPU
+(the path has no cross-GPU exchange); value = all ranks' codewords / the slowest rank's
+time.  --impl reference times the CPU oracle (the plain C implementation used by the
+tests) on bounded samples of the same workload, on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+POPC_PER_SM_PER_CLK = 16          # measured on GB300 (popc.b32 throughput per SM per clock)
+NOMINAL_SMS = 152
+NOMINAL_MAX_MHZ = 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="rand200x100")
+    ap.add_argument("--max-stage", type=int, default=10)
+    ap.add_argument("--filter", type=int, default=1)
+    ap.add_argument("--time-to-d", action="store_true", help="also run the full computation once (time-to-d)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--verbose", action="store_true", help="per-level records on stderr")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------- helpers ---
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------ CPU oracle ---
+
+def oracle_sample_rate(G, n, k, g, seconds, threads):
+    """Codewords/s of the CPU oracle on a bounded prefix of level (g, 0), sized to take
+    about `seconds` on `threads` threads.  Returns (rate, codewords, seconds)."""
+    import oracle
+    gams, _, _ = oracle.gammas(G, n, k)
+    total = math.comb(k, g)
+    probe = min(total, 2_000_000 * threads)
+    t0 = time.perf_counter()
+    oracle.scan(gams[0], n, k, g, 0, probe, threads=threads)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    size = min(total, max(probe, int(probe / dt * seconds)))
+    t0 = time.perf_counter()
+    oracle.scan(gams[0], n, k, g, 0, size, threads=threads)
+    dt = time.perf_counter() - t0
+    return size / dt, size, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1911_08963_gb300 import inputs
+    oracle.build()
+    G, n, k = inputs.single_code(args.workload)
+    threads = os.cpu_count() or 1
+    g = args.max_stage
+    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    rates = []
+    for i in range(args.warmup + args.steps):
+        rate, size, dt = oracle_sample_rate(G, n, k, g, per_step, threads)
+        if i >= args.warmup:
+            rates.append((size, dt))
+    cw = sum(s for s, _ in rates)
+    sec = sum(t for _, t in rates)
+    value = cw / sec
+    line = {
+        "impl": "reference", "metric": "codewords/s", "value": value, "unit": "codewords/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / len(rates),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic: random code G=[I_k|R], R from SplitMix64 seed (first invertible draw)",
+        "config": {"workload": "%s: level g=%d of Gamma_1, colex prefix of %d combinations per step "
+                               "(CPU oracle, bounded sample)" % (args.workload, g, rates[0][0]),
+                   "n": n, "k": k},
+        "cpu_baseline": {"value": value, "unit": "codewords/s", "cores": threads, "kind": "oracle",
+                         "sample": "colex-rank prefix of level (g=%d, Gamma_1), %d combinations per step"
+                                   % (g, rates[0][0])},
+        "e2e": {"value": value, "unit": "codewords/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------- GPU arm -------
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py: no CUDA device (the GPU path has no CPU fallback)")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1911_08963_gb300 import binding as B
+    from paper_1911_08963_gb300 import inputs
+
+    G, n, k = inputs.single_code(args.workload)
+    stream = torch.cuda.current_stream()
+    opt = B.md_options_init(max_stage=args.max_stage, filter=args.filter, stream=stream.cuda_stream)
+    h = B.md_create(G, n, k, opt)
+    l2_flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+
+    def step():
+        d, wit = B.md_compute(h, n)
+        return d, B.md_info_get(h), B.md_levels(h, with_time=True)
+
+    for _ in range(args.warmup):
+        step()
+        l2_flush.zero_()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
+                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    sampler.start()
+    ev = []
+    infos = []
+    lev_all = []
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        d, info, levels = step()
+        e1.record(stream)
+        ev.append((e0, e1))
+        infos.append(info)
+        lev_all.append(levels)
+        l2_flush.zero_()                  # outside the events: the next step starts with a cold L2
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    total_s = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
+    cw = sum(i["codewords"] for i in infos)
+    launches = sum(i["gpu_launches"] for i in infos)
+    if ws > 1:
+        t = torch.tensor([total_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_s = float(t.item())
+        c = torch.tensor([float(cw)], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(c)
+        cw = int(c.item())
+    value = cw / total_s
+
+    # roofline of the dominant kernel: the enumeration kernels of the deepest stage
+    top_g = max(lv[0] for lv in lev_all[0])
+    top = [lv for levels in lev_all for lv in levels if lv[0] == top_g]
+    top_cw = sum(lv[4] for lv in top)
+    top_s = sum(lv[5] for lv in top)
+    per_launch_cw = top_cw / len(top)
+    per_launch_s = top_s / len(top)
+    peak = POPC_PER_SM_PER_CLK * NOMINAL_SMS * NOMINAL_MAX_MHZ * 1e6 / 1e9       # Gpopc/s
+    achieved = per_launch_cw * 1.0 / per_launch_s / 1e9                              # 1 popc per codeword (filtered)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpopc/s", "frac": achieved / peak,
+                "traffic": None,
+                "kernel": "split_kernel (stage g=%d levels, %d launches timed)" % (top_g, len(top)),
+                "peak_basis": "16 popc/clk/SM (measured) x 152 SMs x 2070 MHz max clock",
+                "work_basis": "1 popc per codeword: popcount of the OR of the packed words, exact weight "
+                              "only for codewords that can reach U"}
+
+    line = {
+        "metric": "codewords/s", "value": value, "unit": "codewords/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic: random code G=[I_100|R], R i.i.d. Bernoulli(1/2) from SplitMix64 seed 3",
+        "config": {"workload": "random [200,100] seed 3, Brouwer-Zimmermann stages g=1..%d, every level "
+                               "complete (%d codewords per step)" % (args.max_stage, infos[0]["codewords"]),
+                   "n": n, "k": k, "max_stage": args.max_stage, "filter": args.filter,
+                   "l2": "flushed between steps (512 MiB write); inputs are ~100 KB",
+                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
+        "d_after_stages": infos[0]["d"],
+    }
+
+    if rank == 0 and not args.no_e2e:
+        # end to end through the C ABI from host buffers: create (host G), compute, destroy
+        opt_e = B.md_options_init(max_stage=args.max_stage, filter=args.filter)
+        hh = B.md_create(G, n, k, opt_e)
+        B.md_compute(hh, n)
+        B.md_destroy(hh)
+        times, h2d, d2h, cwe = [], 0, 0, 0
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            hh = B.md_create(G, n, k, opt_e)
+            B.md_compute(hh, n)
+            inf = B.md_info_get(hh)
+            B.md_destroy(hh)
+            times.append(time.perf_counter() - t0)
+            h2d += inf["h2d_bytes"] + G.nbytes
+            d2h += inf["d2h_bytes"]
+            cwe += inf["codewords"]
+        line["e2e"] = {"value": cwe / sum(times), "unit": "codewords/s",
+                       "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        threads = os.cpu_count() or 1
+        rate, size, dt = oracle_sample_rate(G, n, k, args.max_stage, args.cpu_seconds, threads)
+        line["cpu_baseline"] = {"value": rate, "unit": "codewords/s", "cores": threads, "kind": "oracle",
+                                "sample": "colex-rank prefix of level (g=%d, Gamma_1): %d combinations, %.1f s"
+                                          % (args.max_stage, size, dt)}
+
+    if rank == 0 and args.time_to_d:
+        opt_f = B.md_options_init(filter=args.filter, stream=stream.cuda_stream)
+        hf = B.md_create(G, n, k, opt_f)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        dfull, wit = B.md_compute(hf, n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        inf = B.md_info_get(hf)
+        B.md_destroy(hf)
+        line["time_to_d"] = {"d": dfull, "seconds_device": e0.elapsed_time(e1) * 1e-3, "seconds_wall": wall,
+                             "codewords": inf["codewords"], "stop_stage": inf["stop_g"],
+                             "complete": inf["complete"]}
+
+    if args.verbose and rank == 0:
+        for lv in lev_all[0]:
+            sys.stderr.write("level g=%d j=%d weight=%d rank=%d count=%d kernel=%.4f s  %.3e cw/s\n"
+                             % (lv[0], lv[1], lv[2], lv[3], lv[4], lv[5], lv[4] / max(lv[5], 1e-9)))
+    B.md_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -76,6 +76,10 @@ typedef struct md_options {
     void *stream;             /* cudaStream_t to run on; NULL = the library's own stream */
     volatile int *cancel_flag;/* optional host flag (pinned or ordinary memory): set non-zero
                                  to cancel; polled between stages */
+    int batch_mode;           /* md_batch only: 0 (default) = all codes in one persistent
+                                 round schedule; 1 = one md_compute per code, in order */
+    int use_graph;            /* md_batch only: 1 (default) = capture the round schedule in a
+                                 CUDA graph and launch it once; 0 = plain stream launches */
 } md_options;
 
 /* Result details of the last md_compute on a handle. */
@@ -94,6 +98,8 @@ typedef struct md_info {
     double seconds_total;          /* wall time of md_compute */
     double seconds_device;         /* device time of the enumeration kernels */
     int gpu_launches;              /* kernels launched by the last md_compute */
+    uint64_t h2d_bytes;            /* host-to-device bytes copied by the last md_compute */
+    uint64_t d2h_bytes;            /* device-to-host bytes copied by the last md_compute */
 } md_info;
 
 /* One processed level: stage g, matrix j, and the least weight of that level with its
@@ -106,6 +112,7 @@ typedef struct md_level {
     int pad;
     uint64_t first_rank;
     uint64_t count;                /* C(k, g) */
+    double seconds;                /* device time of the level's enumeration kernel */
 } md_level;
 
 /* Fill *opt with defaults.  Always MD_OK (MD_EINVAL for NULL). */
@@ -139,18 +146,50 @@ int md_gamma(md_handle h, int j, uint64_t *gamma, int *order);
 int md_scan_range(md_handle h, int g, int j, uint64_t r0, uint64_t r1, int bound,
                   int *weight, uint64_t *first_rank);
 
+/* Least weight over one task of level (g, j), g >= 5, computed by the production
+   enumeration kernel: all combinations c_1 < ... < c_g whose element c_{P+1} equals M and
+   whose upper elements (c_{P+2}, ..., c_g), as a subset of {M+1, ..., k-1}, have colex
+   index in [u0, u1).  P = 2 for g = 5 and P = 3 for g >= 6; the heads (c_1..c_P) range
+   over every P-subset of {0..M-1}.  This is the analogue of the paper's prefix task
+   (Section 3.1, Process_prefix) for the colex-ordered decomposition the kernels use.
+   bound as in md_scan_range.  MD_EINVAL if M is outside [P, k - 1 - (g - P - 1)]. */
+int md_scan_task(md_handle h, int g, int j, int M, uint64_t u0, uint64_t u1, int bound,
+                 int *weight, uint64_t *first_rank);
+
+/* The work decomposition of level (g, j) that md_compute uses (host-only, no device
+   work).  *kind: 0 = per-lane colex rank ranges (small levels), 2 or 3 = the head size P
+   of the split enumeration.  For kind 2/3 each entry i describes the tasks with
+   c_{P+1} = M: tasks[i] = {M, number of upper parts, upper parts per lane, first work
+   item}; *count receives the number of entries (at most max written); for kind 0,
+   *count = 0.  *work_items receives the number of work items of the level. */
+typedef struct md_task_info {
+    uint32_t M;
+    uint32_t per_lane;
+    uint64_t uppers;
+    uint64_t first_item;
+} md_task_info;
+
+int md_level_plan(md_handle h, int g, int j, int *kind, md_task_info *tasks, int max, int *count,
+                  uint64_t *work_items);
+
 void md_destroy(md_handle h);
 
 /* Static text for a status code. */
 const char *md_strerror(int code);
 
 /* ---- batched codes ------------------------------------------------------------------
- * md_batch runs many codes of uneven n, k to completion in persistent launches: each
- * code keeps its own U, L, stage and level records on the device, and idle warps steal
- * work from any code.  codes[i].G follows the packing rule above.  d[i] and status[i]
- * are written per code; witness (may be NULL) receives code i's witness at word offset
- * sum_{t<i} ceil(n_t/64).  Returns MD_OK if the batch ran (per-code errors are in
- * status[]), or an error for the whole call. */
+ * md_batch runs many codes of uneven n, k to completion in one schedule: each code keeps
+ * its own U, L, stage and level records on the device (its own Alg. 1 state machine);
+ * round r enumerates level r of every code still running, with the work items of all
+ * codes pooled behind shared atomic tickets, so idle warps take work from any code.  The
+ * rounds are captured in a CUDA graph (md_options.use_graph) and launched at once.
+ * codes[i].G follows the packing rule above.  d[i] and status[i] are written per code;
+ * witness (may be NULL) receives code i's witness at word offset sum_{t<i} ceil(n_t/64).
+ * Results are identical to md_compute on each code.  Per-code status: MD_OK (d exact),
+ * MD_EINVAL / MD_ERANK / MD_EUNSUPPORTED for that code's G, MD_EBUDGET if its estimated
+ * work exceeds opt->work_budget (not run; d = -1) or if opt->max_stage stopped it early
+ * (d = the best weight found).  Returns MD_OK if the batch ran, or an error for the whole
+ * call (MD_EINVAL for NULL arguments, MD_ECUDA, MD_ENOMEM). */
 typedef struct md_code {
     const uint64_t *G;
     int n, k;

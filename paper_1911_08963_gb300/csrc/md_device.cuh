@@ -1,0 +1,369 @@
+// md_device.cuh -- device building blocks of the enumeration, shared by the single-code
+// kernels (md_kernels.cu) and the batched kernels (md_batch.cu).
+//
+// Every codeword is a sum of g rows of a systematic matrix Gamma_j (Section 2.1); its
+// weight tightens U (Alg. 1).  A combination c_1 < ... < c_g with colex rank
+// sum_i C(c_i, i) (the paper's "left-lexicographical" order, Section 3.1) is split into
+// head (c_1..c_P), pivot M = c_{P+1} and an upper part (c_{P+2}..c_g): for a fixed M and
+// upper part the heads occupy a contiguous run of C(M, P) ranks starting at
+// C(M, P+1) + sum_{i>P+1} C(c_i, i).  Lanes hold distinct upper parts; the warp walks the
+// heads in lockstep against pre-added pair sums (the right combinations of the paper's
+// saved-additions composition, Section 2.2.1).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "md_internal.h"
+
+namespace mdl {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kInf = 0x3fffffff;
+
+__device__ __forceinline__ unsigned long long binom_d(const unsigned long long *tb, int stride, int a, int b) {
+    return (b < 0 || b > a) ? 0ull : __ldg(tb + (size_t)a * stride + b);
+}
+
+// Row sources: packed rows of WP words, W of them used (the rest are zero padding).
+template <int W, int WP>
+struct SmemSrc {           // rows in shared memory, read with explicit ld.shared
+    uint32_t base;         // shared-window address of row 0
+    __device__ __forceinline__ void load(int idx, uint32_t (&r)[W]) const {
+        const uint32_t a = base + (uint32_t)idx * (WP * 4);
+        if constexpr (WP == 1) {
+            asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r[0]) : "r"(a));
+        } else if constexpr (WP == 2) {
+            uint32_t x, y;
+            asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(x), "=r"(y) : "r"(a));
+            r[0] = x;
+            if constexpr (W > 1) r[1] = y;
+        } else {
+            uint32_t x, y, z, w;
+            asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a));
+            r[0] = x;
+            if constexpr (W > 1) r[1] = y;
+            if constexpr (W > 2) r[2] = z;
+            if constexpr (W > 3) r[3] = w;
+            if constexpr (WP == 8) {
+                asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(x), "=r"(y), "=r"(z), "=r"(w) : "r"(a + 16));
+                if constexpr (W > 4) r[4] = x;
+                if constexpr (W > 5) r[5] = y;
+                if constexpr (W > 6) r[6] = z;
+                if constexpr (W > 7) r[7] = w;
+            }
+        }
+    }
+};
+
+template <int W, int WP>
+struct GlobSrc {           // rows in global memory (read-only path)
+    const uint32_t *p;
+    __device__ __forceinline__ void load(int idx, uint32_t (&r)[W]) const {
+        const uint32_t *q = p + (size_t)idx * WP;
+        if constexpr (WP == 1) {
+            r[0] = __ldg(q);
+        } else if constexpr (WP == 2) {
+            uint2 t = __ldg(reinterpret_cast<const uint2 *>(q));
+            r[0] = t.x;
+            if constexpr (W > 1) r[1] = t.y;
+        } else {
+            uint4 t = __ldg(reinterpret_cast<const uint4 *>(q));
+            r[0] = t.x;
+            if constexpr (W > 1) r[1] = t.y;
+            if constexpr (W > 2) r[2] = t.z;
+            if constexpr (W > 3) r[3] = t.w;
+            if constexpr (WP == 8) {
+                uint4 u = __ldg(reinterpret_cast<const uint4 *>(q + 4));
+                if constexpr (W > 4) r[4] = u.x;
+                if constexpr (W > 5) r[5] = u.y;
+                if constexpr (W > 6) r[6] = u.z;
+                if constexpr (W > 7) r[7] = u.w;
+            }
+        }
+    }
+};
+
+template <int W>
+__device__ __forceinline__ int weight_xor(const uint32_t (&T)[W], const uint32_t (&h)[W]) {
+    int s = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) s += __popc(T[w] ^ h[w]);
+    return s;
+}
+
+// Lower bound of the weight: popc of the OR of the words (one POPC for all W words).
+template <int W>
+__device__ __forceinline__ int weight_lb_or(const uint32_t (&T)[W], const uint32_t (&h)[W]) {
+    uint32_t o = T[0] ^ h[0];
+#pragma unroll
+    for (int w = 1; w < W; w++) o |= T[w] ^ h[w];
+    return __popc(o);
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_xor_sync(kFull, x, o);
+        x = y < x ? y : x;
+    }
+    return x;
+}
+
+// A lane's running best inside one work item (ranks ascend within a lane, so strict
+// improvement keeps the first rank) and the largest packed weight it still has to resolve:
+// thr = min(U, best - 1) - base, or -1 when the lane has nothing to do.
+struct LaneBest {
+    int w = kInf;
+    unsigned long long rank = 0;
+};
+
+// Walk pair-table entries [0, n2) against the lane sum T.
+template <int W, int WP, bool FILTER, class H2Src>
+__device__ __forceinline__ void walk_pairs(const H2Src &h2, const uint32_t (&T)[W], int n2, int &thr, int base,
+                                           LaneBest &best, unsigned long long rbase) {
+    int i = 0;
+    for (; i + 8 <= n2; i += 8) {
+        int lbmin = kInf;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            uint32_t h[W];
+            h2.load(i + u, h);
+            const int lb = FILTER ? weight_lb_or<W>(T, h) : weight_xor<W>(T, h);
+            lbmin = min(lbmin, lb);
+        }
+        if (__any_sync(kFull, lbmin <= thr)) {
+            if (lbmin <= thr) {
+#pragma unroll 1
+                for (int u = 0; u < 8; u++) {
+                    uint32_t h[W];
+                    h2.load(i + u, h);
+                    const int w = weight_xor<W>(T, h);
+                    if (w <= thr) {
+                        best.w = w + base;
+                        best.rank = rbase + (unsigned long long)(i + u);
+                        thr = w - 1;
+                    }
+                }
+            }
+        }
+    }
+    if (i < n2) {
+#pragma unroll 1
+        for (; i < n2; i++) {
+            uint32_t h[W];
+            h2.load(i, h);
+            const int w = weight_xor<W>(T, h);
+            if (w <= thr) {
+                best.w = w + base;
+                best.rank = rbase + (unsigned long long)i;
+                thr = w - 1;
+            }
+        }
+    }
+}
+
+// Level-constant parameters of a chunk.
+struct ChunkCtx {
+    int k, g, v, base, filter_max;
+    const unsigned long long *tb;
+    int stride;
+};
+
+// One work item of a split level: the upper parts of one M entry assigned to this warp.
+// U: the code's shared upper bound (read for thresholds, atomicMin'd on improvement).
+template <int W, int WP, int P, class RowSrc, class H2Src>
+__device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, unsigned long long chunk,
+                                            const RowSrc &rows, const H2Src &h2, unsigned int *U, int &Usnap,
+                                            LaneBest &best) {
+    const int lane = threadIdx.x & 31;
+    const int M = (int)e.M;
+    const unsigned long long per_lane = e.per_lane;
+    const unsigned long long u0 = (chunk - e.chunk_begin) * 32ull * per_lane;
+    const unsigned long long uend = min(u0 + 32ull * per_lane, (unsigned long long)e.uppers);
+    const unsigned long long my_lo = u0 + (unsigned long long)lane * per_lane;
+    const unsigned long long my_hi = min(my_lo + per_lane, uend);
+    const long long nup = my_hi > my_lo ? (long long)(my_hi - my_lo) : 0;
+    const int v = c.v;
+    const int Kp = c.k - 1 - M;
+
+    int el[kMaxG];
+    uint32_t S[W];
+    unsigned long long Rhi = 0;
+#pragma unroll
+    for (int w = 0; w < W; w++) S[w] = 0;
+    if (nup > 0) {
+        // colex unranking of this lane's first upper part (v elements of [0, K'))
+        unsigned long long r = e.upper_base + my_lo;
+        int top = Kp - 1;
+        for (int t = v; t >= 1; t--) {
+            int l2 = t - 1, h = top;
+            while (l2 < h) {
+                const int mid = (l2 + h + 1) >> 1;
+                if (binom_d(c.tb, c.stride, mid, t) <= r) l2 = mid; else h = mid - 1;
+            }
+            el[t - 1] = l2;
+            r -= binom_d(c.tb, c.stride, l2, t);
+            top = l2 - 1;
+        }
+        uint32_t rw[W];
+        rows.load(M, rw);
+#pragma unroll
+        for (int w = 0; w < W; w++) S[w] = rw[w];
+        Rhi = binom_d(c.tb, c.stride, M, P + 1);
+        for (int t = 0; t < v; t++) {
+            const int col = M + 1 + el[t];
+            rows.load(col, rw);
+#pragma unroll
+            for (int w = 0; w < W; w++) S[w] ^= rw[w];
+            Rhi += binom_d(c.tb, c.stride, col, P + 2 + t);
+        }
+    }
+
+    for (long long it = 0; it < (long long)per_lane; ++it) {
+        const bool on = it < nup;
+        if (!__any_sync(kFull, on)) break;
+        int thr = on ? min(Usnap, best.w - 1) - c.base : -1;
+        const bool filt = __all_sync(kFull, thr <= c.filter_max);
+        if constexpr (P == 2) {
+            const int n2 = M * (M - 1) / 2;
+            if (filt) walk_pairs<W, WP, true>(h2, S, n2, thr, c.base, best, Rhi);
+            else walk_pairs<W, WP, false>(h2, S, n2, thr, c.base, best, Rhi);
+        } else {
+            for (int c3 = 2; c3 < M; c3++) {
+                uint32_t T[W], rw[W];
+                rows.load(c3, rw);
+#pragma unroll
+                for (int w = 0; w < W; w++) T[w] = S[w] ^ rw[w];
+                const int n2 = c3 * (c3 - 1) / 2;
+                const unsigned long long rb = Rhi + (unsigned long long)c3 * (c3 - 1) * (c3 - 2) / 6;
+                if (filt) walk_pairs<W, WP, true>(h2, T, n2, thr, c.base, best, rb);
+                else walk_pairs<W, WP, false>(h2, T, n2, thr, c.base, best, rb);
+            }
+        }
+        // next upper part in colex order: the left-most element that can move up moves,
+        // the ones below it reset (shifted coordinates, bound K')
+        if (on && it + 1 < nup) {
+            int t = 0;
+            while (t < v - 1 && el[t] + 1 >= el[t + 1]) t++;
+            uint32_t rw[W];
+            for (int s = 0; s <= t; s++) {
+                const int col = M + 1 + el[s];
+                rows.load(col, rw);
+#pragma unroll
+                for (int w = 0; w < W; w++) S[w] ^= rw[w];
+                Rhi -= binom_d(c.tb, c.stride, col, P + 2 + s);
+            }
+            el[t] += 1;
+            for (int s = 0; s < t; s++) el[s] = s;
+            for (int s = 0; s <= t; s++) {
+                const int col = M + 1 + el[s];
+                rows.load(col, rw);
+#pragma unroll
+                for (int w = 0; w < W; w++) S[w] ^= rw[w];
+                Rhi += binom_d(c.tb, c.stride, col, P + 2 + s);
+            }
+        }
+        const int Ug = (int)*(volatile unsigned int *)U;
+        Usnap = min(Usnap, Ug);
+        if (best.w < Usnap) {
+            atomicMin(U, (unsigned int)best.w);
+            Usnap = best.w;
+        }
+    }
+}
+
+// One work item of a small level: each lane walks its own run of colex ranks [lo, hi)
+// with the colex successor, updating the row sum by the rows that leave and enter.
+template <int W, int WP, class RowSrc>
+__device__ __forceinline__ void simple_chunk(const ChunkCtx &c, unsigned long long lo, unsigned long long hi,
+                                             const RowSrc &rows, unsigned int *U, int &Usnap, LaneBest &best) {
+    const int g = c.g;
+    if (lo < hi) {
+        int cc[kMaxG];
+        unsigned long long r = lo;
+        int top = c.k - 1;
+        for (int t = g; t >= 1; t--) {
+            int l2 = t - 1, h = top;
+            while (l2 < h) {
+                const int mid = (l2 + h + 1) >> 1;
+                if (binom_d(c.tb, c.stride, mid, t) <= r) l2 = mid; else h = mid - 1;
+            }
+            cc[t - 1] = l2;
+            r -= binom_d(c.tb, c.stride, l2, t);
+            top = l2 - 1;
+        }
+        uint32_t acc[W], rw[W];
+#pragma unroll
+        for (int w = 0; w < W; w++) acc[w] = 0;
+        for (int t = 0; t < g; t++) {
+            rows.load(cc[t], rw);
+#pragma unroll
+            for (int w = 0; w < W; w++) acc[w] ^= rw[w];
+        }
+        int thr = min(Usnap, best.w - 1) - c.base;
+        for (unsigned long long rank = lo; rank < hi; ++rank) {
+            int s = 0;
+#pragma unroll
+            for (int w = 0; w < W; w++) s += __popc(acc[w]);
+            if (s <= thr) {
+                best.w = s + c.base;
+                best.rank = rank;
+                thr = s - 1;
+            }
+            if (rank + 1 < hi) {
+                int t = 0;
+                while (t < g - 1 && cc[t] + 1 >= cc[t + 1]) t++;
+                for (int q = 0; q <= t; q++) {
+                    rows.load(cc[q], rw);
+#pragma unroll
+                    for (int w = 0; w < W; w++) acc[w] ^= rw[w];
+                }
+                cc[t] += 1;
+                for (int q = 0; q < t; q++) cc[q] = q;
+                for (int q = 0; q <= t; q++) {
+                    rows.load(cc[q], rw);
+#pragma unroll
+                    for (int w = 0; w < W; w++) acc[w] ^= rw[w];
+                }
+            }
+        }
+    }
+    const int Ug = (int)*(volatile unsigned int *)U;
+    Usnap = min(Usnap, Ug);
+    if (best.w < Usnap) {
+        atomicMin(U, (unsigned int)best.w);
+        Usnap = best.w;
+    }
+}
+
+// Warp min of (weight << 55 | rank) and one atomicMin into the level key.
+__device__ __forceinline__ void publish(unsigned long long *key, const LaneBest &best) {
+    unsigned long long x = best.w < kInf ? (((unsigned long long)best.w << kRankBits) | best.rank) : kNoKey;
+    x = warp_min_u64(x);
+    if ((threadIdx.x & 31) == 0 && x != kNoKey) atomicMin(key, x);
+}
+
+// Work item -> M entry (binary search on the first work item of each entry).
+__device__ __forceinline__ int find_entry(const MEntry *mtab, int n_m, unsigned long long chunk) {
+    int lo = 0, hi = n_m - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&mtab[mid].chunk_begin) <= chunk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void stage_to_smem(uint32_t *dst, const uint32_t *src, int nwords) {
+    const int n4 = nwords / 4;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = __ldg(s4 + i);
+    for (int i = 4 * n4 + threadIdx.x; i < nwords; i += blockDim.x) dst[i] = __ldg(src + i);
+}
+
+}  // namespace dev
+}  // namespace mdl

@@ -1,0 +1,85 @@
+// md_engine.h -- host side of the multi-code engine shared by md_batch and the server.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "md_internal.h"
+
+namespace mdl {
+
+// A code ready for the engine: Gamma matrices and the plans of every level it may run.
+struct PreparedCode {
+    Code code;
+    std::vector<LevelPlan> plans;   // level l = (g - 1) * m + j
+    int g_limit = 0;
+    int max_stage = 0;
+    size_t header_bytes = 0;        // rows, level table, work tables, keys
+    size_t h2_bytes = 0;            // pair tables
+};
+
+// Validate G, build the Gamma_j, check the work budget (estimated combinations) and plan
+// the levels.  Returns an MD_* status for this code.
+int prepare_code(const uint64_t *G, int n, int k, const PlanOptions &po, int max_stage, uint64_t budget,
+                 PreparedCode *out);
+
+// Per-code outcome read back from the engine.
+struct CodeResult {
+    int status = MD_OK;
+    int d = -1;
+    bool complete = false;
+    std::vector<uint64_t> witness;
+};
+
+class Engine {
+  public:
+    Engine() = default;
+    ~Engine();
+    Engine(const Engine &) = delete;
+    Engine &operator=(const Engine &) = delete;
+
+    // Slot tables for up to nslots resident codes; quota = work items per slot per tick
+    // (0 = a whole level per tick).
+    int init(int nslots, cudaStream_t stream, unsigned long long quota, int blocks_per_sm_cap);
+
+    // Place codes in slots with one device allocation for all of them (owned by the
+    // engine until release_all).  Uploads rows and tables, builds pair tables.
+    int load_many(const std::vector<PreparedCode *> &codes, const std::vector<int> &slots);
+    // Place one code in a slot with its own device allocation (released by release).
+    int load_one(PreparedCode &code, int slot);
+
+    // Enqueue one tick (prepare, one round per row width present, post).
+    int tick();
+    // Copy the slot states to the host (synchronises the stream).
+    int read_states(std::vector<BState> &out);
+    // Result of the code in `slot` (its keys are read back); state from read_states.
+    int collect(int slot, const PreparedCode &code, const BState &st, CodeResult *res);
+    // Free a slot (and its own allocation, if load_one placed it).
+    int release(int slot);
+    void release_all();
+
+    int nslots() const { return nslots_; }
+    cudaStream_t stream() const { return stream_; }
+    int launches() const { return launches_; }
+    void set_wclass(int W) { wclass_[W] = true; }
+
+  private:
+    int write_slot(int slot, const BCode &bc, const BState &bs);
+    int fill_code(PreparedCode &pc, char *header, char *h2, std::vector<char> &img, size_t img_off,
+                  BCode *bc);
+    cudaStream_t stream_ = nullptr;
+    int nslots_ = 0;
+    char *tables_ = nullptr;
+    EngineArgs args_{};
+    std::vector<char *> own_mem_;   // per slot, allocations made by load_one
+    std::vector<char *> shared_mem_;
+    bool wclass_[kWClasses] = {false};
+    int blocks_[kWClasses] = {0};
+    int launches_ = 0;
+    int sms_ = 0;
+    int cap_ = 0;
+    std::vector<BCode> host_codes_;
+};
+
+}  // namespace mdl

@@ -1,0 +1,325 @@
+// md_host.cpp -- host-side preparation of a code (Section 2.1 of the paper):
+// validation, rank, disjoint information sets, the systematic matrices Gamma_j, the
+// packing of each Gamma_j for the device, and the per-level work plans.
+//
+// The elimination here is written for the library alone: information sets come from an
+// XOR basis of column vectors, a full-rank Gamma_j is G[:, S_j]^-1 * G, and only the
+// rank-deficient last matrix uses a Gauss-Jordan pass.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "md_internal.h"
+
+namespace mdl {
+
+namespace {
+
+// A vector of up to 256 bits.
+struct Bits {
+    std::array<uint64_t, 4> w{};
+    bool get(int i) const { return (w[i >> 6] >> (i & 63)) & 1u; }
+    void set(int i) { w[i >> 6] |= 1ull << (i & 63); }
+    void flip(int i) { w[i >> 6] ^= 1ull << (i & 63); }
+    void operator^=(const Bits &o) { for (int t = 0; t < 4; t++) w[t] ^= o.w[t]; }
+    bool any() const { return (w[0] | w[1] | w[2] | w[3]) != 0; }
+    int top() const {  // highest set bit or -1
+        for (int t = 3; t >= 0; t--)
+            if (w[t]) return 64 * t + 63 - __builtin_clzll(w[t]);
+        return -1;
+    }
+};
+
+// Column c of G as a k-bit vector (bit i = row i).
+Bits column_of(const std::vector<uint64_t> &G, int nw, int k, int c) {
+    Bits b;
+    for (int i = 0; i < k; i++)
+        if ((G[(size_t)i * nw + c / 64] >> (c % 64)) & 1u) b.set(i);
+    return b;
+}
+
+// XOR basis keyed by the highest set bit; insert() reports whether v was independent.
+struct XorBasis {
+    std::array<Bits, 256> by_top{};
+    std::array<bool, 256> used{};
+    bool insert(Bits v) {
+        for (;;) {
+            int t = v.top();
+            if (t < 0) return false;
+            if (!used[t]) { by_top[t] = v; used[t] = true; return true; }
+            v ^= by_top[t];
+        }
+    }
+};
+
+// Pascal's triangle with saturating addition, rows 0..256.
+struct BinomTable {
+    std::vector<uint64_t> t;  // 257 x 257
+    BinomTable() : t(257 * 257, 0) {
+        for (int a = 0; a <= 256; a++) {
+            t[a * 257] = 1;
+            for (int b = 1; b <= a; b++) {
+                uint64_t x = t[(a - 1) * 257 + b - 1], y = t[(a - 1) * 257 + b];
+                t[a * 257 + b] = (x > UINT64_MAX - y) ? UINT64_MAX : x + y;
+            }
+        }
+    }
+};
+
+const BinomTable &table() {
+    static BinomTable tb;
+    return tb;
+}
+
+}  // namespace
+
+uint64_t binom(int a, int b) {
+    if (a < 0 || b < 0 || b > a) return 0;
+    if (a > 256) return UINT64_MAX;
+    return table().t[a * 257 + b];
+}
+
+// Colex unranking by binary search on C(x, i) (positions i = g..1).
+void colex_unrank(uint64_t r, int g, int k, int *c) {
+    int hi = k - 1;
+    for (int i = g; i >= 1; i--) {
+        int lo = i - 1, h = hi;          // largest x in [lo, h] with C(x, i) <= r
+        while (lo < h) {
+            int mid = (lo + h + 1) / 2;
+            if (binom(mid, i) <= r) lo = mid; else h = mid - 1;
+        }
+        c[i - 1] = lo;
+        r -= binom(lo, i);
+        hi = lo - 1;
+    }
+}
+
+int popcount_row(const uint64_t *row, int nw) {
+    int s = 0;
+    for (int i = 0; i < nw; i++) s += __builtin_popcountll(row[i]);
+    return s;
+}
+
+int lower_bound_after(const Code &c, int g) {
+    int L = 0;
+    for (const Gamma &gm : c.gam) L += std::max(0, g + 1 - (c.k - gm.rank));
+    return L;
+}
+
+namespace {
+
+// Gamma_j = B^-1 G with B = G[:, S] (k x k, invertible): row i of Gamma_j is the sum of
+// the rows t of G with (B^-1)[i][t] = 1, so Gamma_j[:, S[i]] = e_i.
+std::vector<uint64_t> gamma_full(const std::vector<uint64_t> &G, int nw, int k, const std::vector<int> &S) {
+    // rows of [B | I] as bit vectors of length 2k (k <= 128 whenever 2k <= n <= 256)
+    std::vector<Bits> Brow(k), Inv(k);
+    for (int i = 0; i < k; i++) {
+        for (int t = 0; t < k; t++)
+            if ((G[(size_t)i * nw + S[t] / 64] >> (S[t] % 64)) & 1u) Brow[i].set(t);
+        Inv[i].set(i);
+    }
+    for (int col = 0; col < k; col++) {
+        int p = col;
+        while (p < k && !Brow[p].get(col)) p++;
+        std::swap(Brow[col], Brow[p]);
+        std::swap(Inv[col], Inv[p]);
+        for (int i = 0; i < k; i++)
+            if (i != col && Brow[i].get(col)) { Brow[i] ^= Brow[col]; Inv[i] ^= Inv[col]; }
+    }
+    std::vector<uint64_t> out((size_t)k * nw, 0);
+    for (int i = 0; i < k; i++)
+        for (int t = 0; t < k; t++)
+            if (Inv[i].get(t))
+                for (int w = 0; w < nw; w++) out[(size_t)i * nw + w] ^= G[(size_t)t * nw + w];
+    return out;
+}
+
+// Reduced row echelon form with the columns taken in `order` (for the leftover,
+// rank-deficient matrix Gamma_m = [[I, A], [0, B]]).
+std::vector<uint64_t> gamma_rref(const std::vector<uint64_t> &G, int nw, int k, const std::vector<int> &order) {
+    std::vector<uint64_t> A(G);
+    int r = 0;
+    for (int col : order) {
+        if (r == k) break;
+        int p = -1;
+        for (int i = r; i < k; i++)
+            if ((A[(size_t)i * nw + col / 64] >> (col % 64)) & 1u) { p = i; break; }
+        if (p < 0) continue;
+        if (p != r)
+            for (int w = 0; w < nw; w++) std::swap(A[(size_t)p * nw + w], A[(size_t)r * nw + w]);
+        for (int i = 0; i < k; i++)
+            if (i != r && ((A[(size_t)i * nw + col / 64] >> (col % 64)) & 1u))
+                for (int w = 0; w < nw; w++) A[(size_t)i * nw + w] ^= A[(size_t)r * nw + w];
+        r++;
+    }
+    return A;
+}
+
+void pack_gamma(Gamma &gm, int n, int k, int nw) {
+    std::vector<char> in_set(n, 0);
+    if (gm.rank == k)
+        for (int t = 0; t < k; t++) in_set[gm.order[t]] = 1;
+    gm.packed_cols.clear();
+    for (int c = 0; c < n; c++)
+        if (!in_set[c]) gm.packed_cols.push_back(c);
+    gm.weight_base_is_g = (gm.rank == k) ? 1 : 0;
+    int bits = (int)gm.packed_cols.size();
+    gm.W = std::max(1, (bits + 31) / 32);
+    gm.WP = gm.W == 1 ? 1 : gm.W == 2 ? 2 : gm.W <= 4 ? 4 : 8;
+    gm.packed.assign((size_t)k * gm.WP, 0);
+    for (int i = 0; i < k; i++)
+        for (int b = 0; b < bits; b++) {
+            int c = gm.packed_cols[b];
+            if ((gm.rows[(size_t)i * nw + c / 64] >> (c % 64)) & 1u)
+                gm.packed[(size_t)i * gm.WP + b / 32] |= 1u << (b % 32);
+        }
+}
+
+}  // namespace
+
+int build_code(const uint64_t *G, int n, int k, Code *out) {
+    if (!G || !out || n < 1 || k < 1 || k > n) return MD_EINVAL;
+    if (n > kMaxN) return MD_EUNSUPPORTED;
+    const int nw = (n + 63) / 64;
+    for (int i = 0; i < k; i++) {
+        uint64_t last = G[(size_t)i * nw + nw - 1];
+        if (n % 64 && (last >> (n % 64))) return MD_EINVAL;   // padding bits must be zero
+    }
+    Code c;
+    c.n = n; c.k = k; c.nw64 = nw;
+    c.G.assign(G, G + (size_t)k * nw);
+
+    // rank: insert every column into an XOR basis
+    {
+        XorBasis all;
+        int r = 0;
+        for (int col = 0; col < n && r < k; col++)
+            if (all.insert(column_of(c.G, nw, k, col))) r++;
+        if (r < k) return MD_ERANK;
+    }
+
+    // greedy disjoint information sets over the unused columns, ascending
+    std::vector<char> used(n, 0);
+    for (;;) {
+        std::vector<int> remaining;
+        for (int col = 0; col < n; col++)
+            if (!used[col]) remaining.push_back(col);
+        if (remaining.empty()) break;
+        XorBasis basis;
+        std::vector<int> kept;
+        for (int col : remaining) {
+            if ((int)kept.size() == k) break;
+            if (basis.insert(column_of(c.G, nw, k, col))) kept.push_back(col);
+        }
+        Gamma gm;
+        if ((int)kept.size() == k) {
+            gm.rank = k;
+            std::vector<char> in(n, 0);
+            for (int col : kept) { gm.order.push_back(col); in[col] = 1; used[col] = 1; }
+            for (int col = 0; col < n; col++)
+                if (!in[col]) gm.order.push_back(col);
+            gm.rows = gamma_full(c.G, nw, k, kept);
+            c.gam.push_back(std::move(gm));
+            continue;
+        }
+        if (!kept.empty()) {
+            gm.rank = (int)kept.size();
+            std::vector<char> in(n, 0);
+            for (int col : remaining) { gm.order.push_back(col); in[col] = 1; }
+            for (int col = 0; col < n; col++)
+                if (!in[col]) gm.order.push_back(col);
+            gm.rows = gamma_rref(c.G, nw, k, gm.order);
+            c.gam.push_back(std::move(gm));
+        }
+        break;
+    }
+    if ((int)c.gam.size() > MD_MAX_GAMMA) return MD_EUNSUPPORTED;
+    for (Gamma &gm : c.gam) pack_gamma(gm, n, k, nw);
+    *out = std::move(c);
+    return MD_OK;
+}
+
+double estimate_work(const Code &c, int *d_est, int *g_stop) {
+    // expected number of codewords of weight <= w in a random [n, k] code
+    double acc = 0.0;
+    int d = c.n - c.k + 1;
+    for (int w = 1; w <= c.n; w++) {
+        acc += std::exp(std::lgamma(c.n + 1.0) - std::lgamma(w + 1.0) - std::lgamma(c.n - w + 1.0) -
+                        (c.n - c.k) * std::log(2.0));
+        if (acc >= 0.5) { d = w; break; }
+    }
+    d = std::min(d, c.n - c.k + 1);
+    int gs = c.k;
+    for (int g = 1; g <= c.k; g++)
+        if (lower_bound_after(c, g) >= d) { gs = g; break; }
+    double work = 0.0;
+    for (int g = 1; g <= gs; g++) work += (double)c.gam.size() * std::exp(std::lgamma(c.k + 1.0) - std::lgamma(g + 1.0) - std::lgamma(c.k - g + 1.0));
+    if (d_est) *d_est = d;
+    if (g_stop) *g_stop = gs;
+    return work;
+}
+
+int filter_threshold(const Gamma &gm) {
+    const int bits = (int)gm.packed_cols.size();
+    // per bit position b of a 32-bit word: how many packed words have a column there
+    double dist[33] = {1.0};
+    for (int b = 0; b < 32; b++) {
+        int nb = 0;
+        for (int w = 0; w < gm.W; w++)
+            if (32 * w + b < bits) nb++;
+        double p = nb ? 1.0 - std::ldexp(1.0, -nb) : 0.0;
+        for (int t = b + 1; t >= 1; t--) dist[t] = dist[t] * (1 - p) + dist[t - 1] * p;
+        dist[0] *= (1 - p);
+    }
+    double cdf = 0.0;
+    int best = -1;
+    for (int t = 0; t <= 32; t++) {
+        cdf += dist[t];
+        if (cdf < 1e-5) best = t; else break;
+    }
+    return best;
+}
+
+LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o) {
+    LevelPlan p;
+    const Gamma &gm = c.gam[j];
+    const int k = c.k;
+    p.g = g; p.j = j;
+    p.count = binom(k, g);
+    p.base = gm.weight_base_is_g ? g : 0;
+    p.L_after = lower_bound_after(c, g);
+    p.filter_max = o.filter == 0 ? -1 : o.filter == 2 ? 1 << 20 : filter_threshold(gm);
+    const uint64_t target_full = 1ull << std::max(8, std::min(30, o.chunk_log2));
+    // keep at least ~64 work items per SM-sized slice of the level
+    const uint64_t target = std::max<uint64_t>(1ull << 10, std::min<uint64_t>(target_full, p.count / (152ull * 64)));
+    if (g <= 4 || p.count < (1ull << 18) || g > 64) {
+        p.kind = KIND_SIMPLE;
+        p.per_chunk = std::max<uint64_t>(1, target / 32);
+        p.nchunks = (p.count + 32 * p.per_chunk - 1) / (32 * p.per_chunk);
+        return p;
+    }
+    const int P = (g == 5) ? 2 : 3;
+    p.kind = P == 2 ? KIND_SPLIT2 : KIND_SPLIT3;
+    p.v = g - P - 1;
+    uint64_t chunks = 0;
+    for (int M = P; M <= k - 1 - p.v; M++) {
+        MEntry e{};
+        e.M = (uint32_t)M;
+        e.uppers = binom(k - 1 - M, p.v);
+        const uint64_t cost = binom(M, P) + 16;           // codewords + upper-part bookkeeping
+        uint64_t per_lane = (target + 32 * cost - 1) / (32 * cost);
+        per_lane = std::max<uint64_t>(1, std::min<uint64_t>(per_lane, 1u << 30));
+        const uint64_t need = (e.uppers + 31) / 32;       // never more than the lanes can use
+        per_lane = std::min(per_lane, std::max<uint64_t>(1, need));
+        e.per_lane = (uint32_t)per_lane;
+        e.chunk_begin = chunks;
+        chunks += (e.uppers + 32 * per_lane - 1) / (32 * per_lane);
+        p.mtab.push_back(e);
+    }
+    p.nchunks = chunks;
+    return p;
+}
+
+}  // namespace mdl

@@ -1,0 +1,85 @@
+"""GPU: many codes in one schedule (md_batch) give the same d and witness as md_compute on
+each code alone (itself pinned to the oracle), and as the CPU oracle on the small ones."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1911_08963_gb300 import inputs as I
+from tests import textbook as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1911_08963_gb300 import build
+    build.build()
+    from paper_1911_08963_gb300 import binding
+    return binding
+
+
+def single(B, G, n, k):
+    h = B.md_create(G, n, k)
+    try:
+        return B.md_compute(h, n)
+    finally:
+        B.md_destroy(h)
+
+
+def mixed_codes():
+    codes = []
+    for i, (n, k) in enumerate([(20, 7), (48, 16), (64, 18), (100, 33), (90, 45), (126, 42), (31, 10), (80, 38),
+                                (24, 12), (150, 14), (66, 12), (200, 195), (256, 3), (12, 1), (70, 35)]):
+        codes.append((T.pack(T.random_rows(n, k, 100 + i), n), n, k))
+    for name in ("hamming7", "golay24", "rm1_5", "parity10", "trivial6"):
+        rows, n, k = T.TEXTBOOK[name][0]()
+        codes.append((T.pack(rows, n), n, k))
+    return codes
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+def test_batch_matches_single_and_oracle(B, graph):
+    codes = mixed_codes()
+    d, wits, st = B.md_batch(codes, B.md_options_init(use_graph=graph))
+    assert st == [B.MD_OK] * len(codes)
+    for (G, n, k), di, wi in zip(codes, d, wits):
+        ds, ws = single(B, G, n, k)
+        assert di == ds and np.array_equal(wi, ws), (n, k)
+        res = O.bz(G, n, k, threads=8)
+        assert di == res.d and np.array_equal(wi, res.witness), (n, k)
+
+
+def test_batch_per_code_loop_mode(B):
+    codes = mixed_codes()[:8]
+    a = B.md_batch(codes)
+    b = B.md_batch(codes, B.md_options_init(batch_mode=1))
+    assert a[0] == b[0] and a[2] == b[2]
+    assert all(np.array_equal(x, y) for x, y in zip(a[1], b[1]))
+
+
+def test_batch_statuses(B):
+    good = mixed_codes()[:3]
+    rows = T.random_rows(30, 8, 7)
+    bad_rank = (T.pack(rows[:7] + [rows[0] ^ rows[1]], 30), 30, 8)
+    bad_pad = good[0][0].copy()
+    bad_pad[0, -1] |= np.uint64(1 << 40)
+    big = I.single_code("rand200x100")
+    codes = good + [bad_rank, (bad_pad, good[0][1], good[0][2]), big]
+    d, wits, st = B.md_batch(codes, B.md_options_init(work_budget=10 ** 11))
+    assert st[:3] == [B.MD_OK] * 3
+    assert st[3] == B.MD_ERANK and st[4] == B.MD_EINVAL and st[5] == B.MD_EBUDGET
+    assert d[3] == d[4] == d[5] == -1
+    # a stage limit leaves the code incomplete: best weight found so far, status MD_EBUDGET
+    d2, w2, st2 = B.md_batch([big], B.md_options_init(max_stage=3))
+    res = O.bz(big[0], big[1], big[2], stop_after_g=3)
+    assert st2 == [B.MD_EBUDGET] and d2[0] == res.d and np.array_equal(w2[0], res.witness)
+
+
+def test_batch_workload_sample(B):
+    """The uneven batch workload (n in [48,160], k in [n/3, n/2]), first codes: batch vs single."""
+    codes = [c for c in I.batch_codes(count=40) if c[1] <= 110]
+    d, wits, st = B.md_batch(codes)
+    assert all(s == B.MD_OK for s in st)
+    for (G, n, k), di, wi in zip(codes, d, wits):
+        ds, ws = single(B, G, n, k)
+        assert di == ds and np.array_equal(wi, ws)

@@ -1,0 +1,113 @@
+"""GPU: the continuous-batching server returns, for every request, exactly what md_compute
+returns for that code alone, while requests join and leave the running mix."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1911_08963_gb300 import inputs as I
+from tests import textbook as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1911_08963_gb300 import build
+    build.build()
+    from paper_1911_08963_gb300 import binding
+    return binding
+
+
+def single(B, G, n, k):
+    h = B.md_create(G, n, k)
+    try:
+        return B.md_compute(h, n)
+    finally:
+        B.md_destroy(h)
+
+
+def wait(B, s, ticket, n, timeout=120):
+    t0 = time.time()
+    while time.time() - t0 < timeout:
+        r = B.md_server_poll(s, ticket, n)
+        if r is not None:
+            return r
+        time.sleep(0.0005)
+    raise TimeoutError("request %d did not finish" % ticket)
+
+
+def test_server_results_equal_alone(B):
+    s = B.md_server_create(slots=8)
+    try:
+        codes = [(T.pack(T.random_rows(n, k, 300 + i), n), n, k)
+                 for i, (n, k) in enumerate([(100, 40), (48, 16), (64, 18), (126, 42), (31, 10), (90, 45),
+                                             (80, 38), (150, 14), (20, 7), (66, 12), (57, 19), (96, 44)])]
+        # a large code first, then the others arrive while it runs
+        tickets = [B.md_server_submit(s, G, n, k) for G, n, k in codes]
+        out = [wait(B, s, t, n) for t, (G, n, k) in zip(tickets, codes)]
+        for (G, n, k), (d, wit, st) in zip(codes, out):
+            assert st == B.MD_OK
+            ds, ws = single(B, G, n, k)
+            assert d == ds and np.array_equal(wit, ws)
+        # a ticket is returned once
+        with pytest.raises(B.MDError):
+            B.md_server_poll(s, tickets[0], codes[0][1])
+    finally:
+        B.md_server_destroy(s)
+
+
+def test_server_overlap_small_finishes_before_large(B):
+    s = B.md_server_create(slots=4)
+    try:
+        G, n, k = I.single_code("rand128x64")
+        tl = B.md_server_submit(s, G, n, k)
+        time.sleep(0.01)
+        small = (T.pack(T.random_rows(40, 12, 9), 40), 40, 12)
+        ts = B.md_server_submit(s, *small)
+        d_small = wait(B, s, ts, 40)
+        assert B.md_server_poll(s, tl, n) is None          # the large code is still running
+        d_large = wait(B, s, tl, n)
+        assert d_small[0] == single(B, *small)[0]
+        ds, ws = single(B, G, n, k)
+        assert d_large[0] == ds and np.array_equal(d_large[1], ws)
+    finally:
+        B.md_server_destroy(s)
+
+
+def test_server_rejections(B):
+    s = B.md_server_create(slots=2, work_budget=10 ** 9)
+    try:
+        G, n, k = I.single_code("rand200x100")
+        with pytest.raises(B.MDError) as e:
+            B.md_server_submit(s, G, n, k)
+        assert e.value.code == B.MD_EBUDGET
+        rows = T.random_rows(30, 8, 7)
+        with pytest.raises(B.MDError) as e:
+            B.md_server_submit(s, T.pack(rows[:7] + [rows[0] ^ rows[1]], 30), 30, 8)
+        assert e.value.code == B.MD_ERANK
+        with pytest.raises(B.MDError):
+            B.md_server_poll(s, 12345, 30)
+    finally:
+        B.md_server_destroy(s)
+
+
+def test_server_trace_sample(B):
+    """First requests of the Poisson trace with a work budget: accepted ones equal md_compute."""
+    s = B.md_server_create(slots=16, work_budget=2 * 10 ** 10)
+    try:
+        trace = I.serving_trace(40)
+        tickets = []
+        for t, G, n, k in trace:
+            try:
+                tickets.append((B.md_server_submit(s, G, n, k), G, n, k))
+            except B.MDError as e:
+                assert e.code == B.MD_EBUDGET
+        assert tickets
+        for tk, G, n, k in tickets:
+            d, wit, st = wait(B, s, tk, n)
+            assert st == B.MD_OK
+            ds, ws = single(B, G, n, k)
+            assert d == ds and np.array_equal(wit, ws)
+    finally:
+        B.md_server_destroy(s)

@@ -1,0 +1,156 @@
+"""CPU-side checks of the C ABI library: it loads, exports every entry point declared in
+include/md.h, validates its inputs, and builds the same Gamma_j as the oracle, bit for bit.
+No call here touches the GPU (md_create and md_gamma are host-only)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import textbook as T
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_1911_08963_gb300 import build
+    build.build()
+    from paper_1911_08963_gb300 import binding
+    return binding
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "md.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?\s*(md_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(B):
+    names = declared_functions()
+    assert "md_compute" in names and "md_batch" in names and "md_server_poll" in names
+    missing = [n for n in names if not hasattr(B.lib, n)]
+    assert not missing, missing
+    assert set(names) <= set(B.PROTOTYPES)
+
+
+def test_strerror(B):
+    for code in range(11):
+        assert B.md_strerror(code)
+    assert B.md_strerror(999) == "unknown status"
+
+
+def test_create_validation(B):
+    rows = T.random_rows(40, 10, 1)
+    G = T.pack(rows, 40)
+    h = B.md_create(G, 40, 10)
+    B.md_destroy(h)
+    with pytest.raises(B.MDError) as e:
+        B.md_create(T.pack(rows[:9] + [rows[0] ^ rows[1]], 40), 40, 10)
+    assert e.value.code == B.MD_ERANK
+    bad = G.copy()
+    bad[0, 0] |= np.uint64(1 << 45)                      # a bit beyond column n-1
+    with pytest.raises(B.MDError) as e:
+        B.md_create(bad, 40, 10)
+    assert e.value.code == B.MD_EINVAL
+    big = np.zeros((1, 5), dtype=np.uint64)
+    big[0, 0] = 1
+    with pytest.raises(B.MDError) as e:
+        B.md_create(big, 257, 1)
+    assert e.value.code == B.MD_EUNSUPPORTED
+    p = G.ctypes.data_as(B.u64p)
+    hh = ctypes.c_void_p()
+    assert B.lib.md_create(p, 40, 41, ctypes.byref(hh)) == B.MD_EINVAL
+    assert B.lib.md_create(p, 0, 0, ctypes.byref(hh)) == B.MD_EINVAL
+    assert B.lib.md_create(None, 40, 10, ctypes.byref(hh)) == B.MD_EINVAL
+
+
+@pytest.mark.parametrize("n,k,seed", [(16, 5, 1), (24, 8, 2), (40, 13, 3), (70, 20, 4), (130, 40, 5),
+                                      (64, 32, 6), (9, 9, 7), (33, 1, 8), (200, 100, 9), (256, 100, 10),
+                                      (256, 150, 11), (250, 7, 12), (97, 48, 13), (160, 80, 14)])
+def test_gamma_bit_exact_with_oracle(B, n, k, seed):
+    rows = T.random_rows(n, k, seed)
+    G = T.pack(rows, n)
+    gams, ranks, orders = O.gammas(G, n, k)
+    h = B.md_create(G, n, k)
+    try:
+        info = B.md_info_get(h)
+        assert info["m"] == len(gams) and info["ranks"] == ranks
+        for j in range(len(gams)):
+            rows_j, order_j = B.md_gamma(h, j, n, k)
+            assert order_j == orders[j]
+            assert np.array_equal(rows_j, gams[j]), (n, k, j)
+    finally:
+        B.md_destroy(h)
+
+
+def test_gamma_textbook(B):
+    for name, (ctor, d, _) in T.TEXTBOOK.items():
+        rows, n, k = ctor()
+        G = T.pack(rows, n)
+        gams, ranks, orders = O.gammas(G, n, k)
+        h = B.md_create(G, n, k)
+        try:
+            for j in range(len(gams)):
+                rj, oj = B.md_gamma(h, j, n, k)
+                assert np.array_equal(rj, gams[j]) and oj == orders[j], name
+        finally:
+            B.md_destroy(h)
+
+
+@pytest.mark.parametrize("n,k,g", [(100, 33, 6), (200, 100, 10), (200, 100, 5), (160, 80, 8), (64, 32, 4),
+                                   (256, 150, 6), (48, 24, 7), (128, 64, 7)])
+def test_level_plan_covers_every_combination(B, n, k, g):
+    """The split decomposition covers C(k, g) combinations: sum over M of
+    C(k-1-M, v) upper parts times C(M, P) heads (closed form), work items are contiguous,
+    and every work item holds at most 32 lanes x per_lane upper parts."""
+    import math
+    rows = T.random_rows(n, k, 3)
+    h = B.md_create(T.pack(rows, n), n, k)
+    try:
+        kind, tasks, items = B.md_level_plan(h, g, 0)
+        if g <= 4:
+            assert kind == 0 and tasks == [] and items >= 1
+            return
+        P = kind
+        assert P == (2 if g == 5 else 3)
+        v = g - P - 1
+        total = 0
+        next_item = 0
+        assert [t[0] for t in tasks] == list(range(P, k - v))
+        for M, per_lane, uppers, first in tasks:
+            assert uppers == math.comb(k - 1 - M, v)
+            assert first == next_item
+            next_item += -(-uppers // (32 * per_lane))
+            total += uppers * math.comb(M, P)
+        assert next_item == items
+        assert total == math.comb(k, g)
+    finally:
+        B.md_destroy(h)
+
+
+def test_level_plan_small_enumeration_exact(B):
+    """Tiny level: the combinations generated from the plan (heads below M, M, upper part
+    by colex index) are exactly the g-subsets, each with its colex rank."""
+    import math
+    import itertools
+    n, k, g = 50, 28, 6                  # C(28, 6) = 376740 >= 2^18: a split level
+    h = B.md_create(T.pack(T.random_rows(n, k, 4), n), n, k)
+    try:
+        kind, tasks, items = B.md_level_plan(h, g, 0)
+    finally:
+        B.md_destroy(h)
+    assert kind == 3
+    P = 3
+    v = g - P - 1
+    got = []
+    for M, per_lane, uppers, first in tasks:
+        for u in range(uppers):
+            up = tuple(M + 1 + e for e in O.colex_unrank(u, v, k - 1 - M))
+            for head in itertools.combinations(range(M), P):
+                c = head + (M,) + up
+                got.append((T.colex_rank_formula(c), c))
+    assert sorted(r for r, _ in got) == list(range(math.comb(k, g)))
+    assert sorted(c for _, c in got) == list(itertools.combinations(range(k), g))
