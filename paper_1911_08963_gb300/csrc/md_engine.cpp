@@ -257,6 +257,7 @@ int Engine::load_many(const std::vector<PreparedCode *> &codes, const std::vecto
 }
 
 int Engine::load_one(PreparedCode &pc, int slot) {
+    if (slot < 0 || slot >= nslots_) return MD_EINVAL;
     char *mem = nullptr;
     if (cudaMalloc(&mem, std::max<size_t>(256, pc.header_bytes + pc.h2_bytes)) != cudaSuccess) {
         cudaGetLastError();
@@ -336,6 +337,7 @@ int Engine::collect(int slot, const PreparedCode &pc, const BState &st, CodeResu
 }
 
 int Engine::release(int slot) {
+    if (slot < 0 || slot >= nslots_) return MD_EINVAL;
     BCode off{};
     host_codes_[slot] = off;
     int rc = MD_OK;
@@ -358,6 +360,7 @@ void Engine::release_all() {
     shared_mem_.clear();
     if (tables_) cudaFree(tables_);
     tables_ = nullptr;
+    stream_ = nullptr;                 // the stream belongs to the caller
 }
 
 }  // namespace mdl

@@ -73,7 +73,7 @@ void md_server::run() {
             }
             // admission: free slot and memory budget (a code that fits alone is always admitted
             // when nothing else is resident)
-            while (!pending.empty() && !free_slots.empty()) {
+            while (!pending.empty() && admit.size() < free_slots.size()) {
                 Request &r = pending.front();
                 if (bytes_in_use + r.bytes > opts.device_bytes && !(resident.empty() && admit.empty())) break;
                 bytes_in_use += r.bytes;
