@@ -177,6 +177,37 @@ void md_destroy(md_handle h);
 /* Static text for a status code. */
 const char *md_strerror(int code);
 
+/* ---- rank-range scan without device allocation --------------------------------------
+ * md_scan_range_noalloc computes what md_scan_range computes -- the least weight over the
+ * colex ranks [r0, r1) of the g-row combinations of a matrix, and the first rank reaching
+ * it -- but makes no device allocation and no heap allocation of its own.  It is meant for
+ * callers that cannot allocate: code that runs while a CUDA graph is being captured, real-time
+ * loops that forbid allocation after start-up, and programs whose device memory belongs to
+ * another allocator.
+ * The paper has no counterpart to this entry point.
+ *
+ *   rows         device pointer, 16-byte aligned, owned by the caller: k packed rows of
+ *                `words` 32-bit words each (bit t of word w = packed column 32w + t), stored
+ *                with a row stride of 1, 2, 4, 4, 8, 8, 8, 8 words for words = 1..8; unused
+ *                words and bits must be zero.  Read only.
+ *   weight_base  added to every popcount (g for the non-pivot columns of a full-rank
+ *                Gamma_j, 0 when every column is packed).
+ *   bound        as in md_scan_range (< 0: exact least weight).
+ *   stream       cudaStream_t or NULL; the call synchronises it before returning.
+ *   weight, first_rank  host outputs, as md_scan_range.
+ *
+ * Its device scratch is one fixed array of MD_NOALLOC_SCRATCH_BYTES inside the library;
+ * every GPU that loads the library holds it until the process exits.  The first call on a
+ * device looks the array up and fills its binomial table (make that first call before any
+ * stream capture).  Every call resets the scratch before use, and all calls share it: calls
+ * that overlap on the GPU (from several threads or streams) race and give wrong results.
+ * k > MD_NOALLOC_MAX_K, or more than 2^55 combinations, returns MD_EUNSUPPORTED; a bad
+ * pointer alignment or argument returns MD_EINVAL. */
+#define MD_NOALLOC_MAX_K 128
+#define MD_NOALLOC_SCRATCH_BYTES 139264
+int md_scan_range_noalloc(const uint32_t *rows, int k, int words, int weight_base, int g, uint64_t r0,
+                          uint64_t r1, int bound, void *stream, int *weight, uint64_t *first_rank);
+
 /* ---- batched codes ------------------------------------------------------------------
  * md_batch runs many codes of uneven n, k to completion in one schedule: each code keeps
  * its own U, L, stage and level records on the device (its own Alg. 1 state machine);

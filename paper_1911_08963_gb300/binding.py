@@ -76,6 +76,9 @@ PROTOTYPES = {
                                     ctypes.c_uint64, ctypes.c_int, ip, u64p]),
     "md_level_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ip, ctypes.POINTER(md_task_info),
                                      ctypes.c_int, ip, u64p]),
+    "md_scan_range_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ip,
+                                             u64p]),
     "md_destroy": (None, [ctypes.c_void_p]),
     "md_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "md_batch": (ctypes.c_int, [ctypes.POINTER(md_code), ctypes.c_int, ctypes.POINTER(md_options), ip, u64p, ip]),
@@ -192,6 +195,16 @@ def md_level_plan(h: int, g: int, j: int):
     _check(lib.md_level_plan(h, g, j, ctypes.byref(kind), buf, 512, ctypes.byref(cnt), ctypes.byref(items)),
            "md_level_plan")
     return kind.value, [(t.M, t.per_lane, t.uppers, t.first_item) for t in buf[:cnt.value]], items.value
+
+
+def md_scan_range_noalloc(rows_ptr: int, k: int, words: int, weight_base: int, g: int, r0: int, r1: int,
+                          bound: int = -1, stream=None):
+    """rows_ptr: device address of the packed rows (see include/md.h)."""
+    w = ctypes.c_int()
+    r = ctypes.c_uint64()
+    _check(lib.md_scan_range_noalloc(rows_ptr, k, words, weight_base, g, r0, r1, bound, stream, ctypes.byref(w),
+                                     ctypes.byref(r)), "md_scan_range_noalloc")
+    return w.value, r.value
 
 
 def md_destroy(h: int) -> None:
