@@ -20,6 +20,8 @@ LIB = os.path.join(LIBDIR, "libmd.so")
 SOURCES = ["md_kernels.cu", "md_engine.cu", "md_host.cpp", "md_capi.cpp", "md_engine.cpp", "md_server.cpp", "md_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
+# extra nvcc flags for tuning experiments (e.g. -DMD_UPPERS_PER_LANE=4); empty by default
+COMMON += os.environ.get("MD_NVCC_FLAGS", "").split()
 
 
 def nvcc() -> str:

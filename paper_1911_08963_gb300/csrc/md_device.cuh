@@ -1,5 +1,5 @@
 // md_device.cuh -- device building blocks of the enumeration, shared by the single-code
-// kernels (md_kernels.cu) and the batched kernels (md_batch.cu).
+// kernels (md_kernels.cu) and the multi-code engine (md_engine.cu).
 //
 // Every codeword is a sum of g rows of a systematic matrix Gamma_j (Section 2.1); its
 // weight tightens U (Alg. 1).  A combination c_1 < ... < c_g with colex rank
@@ -22,6 +22,10 @@ namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kInf = 0x3fffffff;
+#ifndef MD_UPPERS_PER_LANE
+#define MD_UPPERS_PER_LANE 2
+#endif
+constexpr int kNU = MD_UPPERS_PER_LANE;       // upper parts a lane walks against each loaded head
 
 __device__ __forceinline__ unsigned long long binom_d(const unsigned long long *tb, int stride, int a, int b) {
     return (b < 0 || b > a) ? 0ull : __ldg(tb + (size_t)a * stride + b);
@@ -113,18 +117,25 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x)
     return x;
 }
 
-// A lane's running best inside one work item (ranks ascend within a lane, so strict
-// improvement keeps the first rank) and the largest packed weight it still has to resolve:
-// thr = min(U, best - 1) - base, or -1 when the lane has nothing to do.
+// A lane's running best inside one work item, as the 64-bit key (weight << 55 | colex rank):
+// the smaller key is the better codeword, and among equal weights the earlier one.
 struct LaneBest {
-    int w = kInf;
-    unsigned long long rank = 0;
+    unsigned long long key = kNoKey;
+    __device__ __forceinline__ int w() const { return key == kNoKey ? kInf : (int)(key >> kRankBits); }
+    __device__ __forceinline__ void offer(int weight, unsigned long long rank) {
+        const unsigned long long k = ((unsigned long long)weight << kRankBits) | rank;
+        if (k < key) key = k;
+    }
 };
 
-// Walk pair-table entries [0, n2) against the lane sum T.
-template <int W, int WP, bool FILTER, class H2Src>
-__device__ __forceinline__ void walk_pairs(const H2Src &h2, const uint32_t (&T)[W], int n2, int &thr, int base,
-                                           LaneBest &best, unsigned long long rbase) {
+// Walk pair-table entries [0, n2) against the NU lane sums T[q].  thr is the largest
+// packed weight the lane still has to resolve, min(U, best) - base (-1: nothing); the
+// exact weights of codewords that pass are offered to the lane's best with their ranks
+// rbase[q] + i.  One loaded entry serves all NU sums (the unrolling of the paper's
+// saved-additions engine, Section 2.2.1: several left combinations share each right one).
+template <int W, int WP, int NU, bool FILTER, class H2Src>
+__device__ __forceinline__ void walk_pairs(const H2Src &h2, const uint32_t (&T)[NU][W], int n2, int &thr, int base,
+                                           LaneBest &best, const unsigned long long (&rbase)[NU]) {
     int i = 0;
     for (; i + 8 <= n2; i += 8) {
         int lbmin = kInf;
@@ -132,8 +143,11 @@ __device__ __forceinline__ void walk_pairs(const H2Src &h2, const uint32_t (&T)[
         for (int u = 0; u < 8; u++) {
             uint32_t h[W];
             h2.load(i + u, h);
-            const int lb = FILTER ? weight_lb_or<W>(T, h) : weight_xor<W>(T, h);
-            lbmin = min(lbmin, lb);
+#pragma unroll
+            for (int q = 0; q < NU; q++) {
+                const int lb = FILTER ? weight_lb_or<W>(T[q], h) : weight_xor<W>(T[q], h);
+                lbmin = min(lbmin, lb);
+            }
         }
         if (__any_sync(kFull, lbmin <= thr)) {
             if (lbmin <= thr) {
@@ -141,28 +155,26 @@ __device__ __forceinline__ void walk_pairs(const H2Src &h2, const uint32_t (&T)[
                 for (int u = 0; u < 8; u++) {
                     uint32_t h[W];
                     h2.load(i + u, h);
-                    const int w = weight_xor<W>(T, h);
-                    if (w <= thr) {
-                        best.w = w + base;
-                        best.rank = rbase + (unsigned long long)(i + u);
-                        thr = w - 1;
+#pragma unroll
+                    for (int q = 0; q < NU; q++) {
+                        const int w = weight_xor<W>(T[q], h);
+                        if (w <= thr) best.offer(w + base, rbase[q] + (unsigned long long)(i + u));
                     }
+                    thr = min(thr, best.w() - base);
                 }
             }
         }
     }
-    if (i < n2) {
 #pragma unroll 1
-        for (; i < n2; i++) {
-            uint32_t h[W];
-            h2.load(i, h);
-            const int w = weight_xor<W>(T, h);
-            if (w <= thr) {
-                best.w = w + base;
-                best.rank = rbase + (unsigned long long)i;
-                thr = w - 1;
-            }
+    for (; i < n2; i++) {
+        uint32_t h[W];
+        h2.load(i, h);
+#pragma unroll
+        for (int q = 0; q < NU; q++) {
+            const int w = weight_xor<W>(T[q], h);
+            if (w <= thr) best.offer(w + base, rbase[q] + (unsigned long long)i);
         }
+        thr = min(thr, best.w() - base);
     }
 }
 
@@ -173,32 +185,17 @@ struct ChunkCtx {
     int stride;
 };
 
-// One work item of a split level: the upper parts of one M entry assigned to this warp.
-// U: the code's shared upper bound (read for thresholds, atomicMin'd on improvement).
-template <int W, int WP, int P, class RowSrc, class H2Src>
-__device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, unsigned long long chunk,
-                                            const RowSrc &rows, const H2Src &h2, unsigned int *U, int &Usnap,
-                                            LaneBest &best) {
-    const int lane = threadIdx.x & 31;
-    const int M = (int)e.M;
-    const unsigned long long per_lane = e.per_lane;
-    const unsigned long long u0 = (chunk - e.chunk_begin) * 32ull * per_lane;
-    const unsigned long long uend = min(u0 + 32ull * per_lane, (unsigned long long)e.uppers);
-    const unsigned long long my_lo = u0 + (unsigned long long)lane * per_lane;
-    const unsigned long long my_hi = min(my_lo + per_lane, uend);
-    const long long nup = my_hi > my_lo ? (long long)(my_hi - my_lo) : 0;
-    const int v = c.v;
-    const int Kp = c.k - 1 - M;
-
+// Colex state of a lane's next upper part (v elements of [0, K'), column M + 1 + element),
+// its row sum and the rank of its first head.
+template <int W, int P, class RowSrc>
+struct UpperWalker {
     int el[kMaxG];
     uint32_t S[W];
-    unsigned long long Rhi = 0;
-#pragma unroll
-    for (int w = 0; w < W; w++) S[w] = 0;
-    if (nup > 0) {
-        // colex unranking of this lane's first upper part (v elements of [0, K'))
-        unsigned long long r = e.upper_base + my_lo;
-        int top = Kp - 1;
+    unsigned long long R;
+
+    __device__ __forceinline__ void start(const ChunkCtx &c, const RowSrc &rows, int M, unsigned long long r) {
+        const int v = c.v;
+        int top = c.k - 1 - M - 1;
         for (int t = v; t >= 1; t--) {
             int l2 = t - 1, h = top;
             while (l2 < h) {
@@ -213,65 +210,108 @@ __device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, 
         rows.load(M, rw);
 #pragma unroll
         for (int w = 0; w < W; w++) S[w] = rw[w];
-        Rhi = binom_d(c.tb, c.stride, M, P + 1);
+        R = binom_d(c.tb, c.stride, M, P + 1);
         for (int t = 0; t < v; t++) {
             const int col = M + 1 + el[t];
             rows.load(col, rw);
 #pragma unroll
             for (int w = 0; w < W; w++) S[w] ^= rw[w];
-            Rhi += binom_d(c.tb, c.stride, col, P + 2 + t);
+            R += binom_d(c.tb, c.stride, col, P + 2 + t);
         }
     }
 
-    for (long long it = 0; it < (long long)per_lane; ++it) {
-        const bool on = it < nup;
+    // colex successor: the left-most element that can move up moves, those below it reset
+    __device__ __forceinline__ void advance(const ChunkCtx &c, const RowSrc &rows, int M) {
+        const int v = c.v;
+        int t = 0;
+        while (t < v - 1 && el[t] + 1 >= el[t + 1]) t++;
+        uint32_t rw[W];
+        for (int s = 0; s <= t; s++) {
+            const int col = M + 1 + el[s];
+            rows.load(col, rw);
+#pragma unroll
+            for (int w = 0; w < W; w++) S[w] ^= rw[w];
+            R -= binom_d(c.tb, c.stride, col, P + 2 + s);
+        }
+        el[t] += 1;
+        for (int s = 0; s < t; s++) el[s] = s;
+        for (int s = 0; s <= t; s++) {
+            const int col = M + 1 + el[s];
+            rows.load(col, rw);
+#pragma unroll
+            for (int w = 0; w < W; w++) S[w] ^= rw[w];
+            R += binom_d(c.tb, c.stride, col, P + 2 + s);
+        }
+    }
+};
+
+// One work item of a split level: the upper parts of one M entry assigned to this warp,
+// NU of them per lane at a time.  U: the code's shared upper bound (read for thresholds,
+// atomicMin'd on improvement).
+template <int W, int WP, int P, int NU, class RowSrc, class H2Src>
+__device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, unsigned long long chunk,
+                                            const RowSrc &rows, const H2Src &h2, unsigned int *U, int &Usnap,
+                                            LaneBest &best) {
+    const int lane = threadIdx.x & 31;
+    const int M = (int)e.M;
+    const unsigned long long per_lane = e.per_lane;
+    const unsigned long long u0 = (chunk - e.chunk_begin) * 32ull * per_lane;
+    const unsigned long long uend = min(u0 + 32ull * per_lane, (unsigned long long)e.uppers);
+    const unsigned long long my_lo = u0 + (unsigned long long)lane * per_lane;
+    const unsigned long long my_hi = min(my_lo + per_lane, uend);
+    long long remaining = my_hi > my_lo ? (long long)(my_hi - my_lo) : 0;
+
+    UpperWalker<W, P, RowSrc> up;
+#pragma unroll
+    for (int w = 0; w < W; w++) up.S[w] = 0;
+    up.R = 0;
+    if (remaining > 0) up.start(c, rows, M, e.upper_base + my_lo);
+
+    for (long long it = 0; it < (long long)per_lane; it += NU) {
+        const bool on = remaining > 0;
         if (!__any_sync(kFull, on)) break;
-        int thr = on ? min(Usnap, best.w - 1) - c.base : -1;
+        // NU upper parts of this lane; past the lane's end the last one is repeated (a repeat
+        // offers the same keys again and cannot change the minimum)
+        uint32_t S[NU][W];
+        unsigned long long R[NU];
+#pragma unroll
+        for (int q = 0; q < NU; q++) {
+#pragma unroll
+            for (int w = 0; w < W; w++) S[q][w] = up.S[w];
+            R[q] = up.R;
+            if (remaining > 0) {
+                remaining--;
+                if (remaining > 0) up.advance(c, rows, M);
+            }
+        }
+        int thr = on ? min(Usnap, best.w()) - c.base : -1;
         const bool filt = __all_sync(kFull, thr <= c.filter_max);
         if constexpr (P == 2) {
             const int n2 = M * (M - 1) / 2;
-            if (filt) walk_pairs<W, WP, true>(h2, S, n2, thr, c.base, best, Rhi);
-            else walk_pairs<W, WP, false>(h2, S, n2, thr, c.base, best, Rhi);
+            if (filt) walk_pairs<W, WP, NU, true>(h2, S, n2, thr, c.base, best, R);
+            else walk_pairs<W, WP, NU, false>(h2, S, n2, thr, c.base, best, R);
         } else {
             for (int c3 = 2; c3 < M; c3++) {
-                uint32_t T[W], rw[W];
+                uint32_t T[NU][W], rw[W];
+                unsigned long long rb[NU];
                 rows.load(c3, rw);
+                const unsigned long long h3 = (unsigned long long)c3 * (c3 - 1) * (c3 - 2) / 6;
 #pragma unroll
-                for (int w = 0; w < W; w++) T[w] = S[w] ^ rw[w];
+                for (int q = 0; q < NU; q++) {
+#pragma unroll
+                    for (int w = 0; w < W; w++) T[q][w] = S[q][w] ^ rw[w];
+                    rb[q] = R[q] + h3;
+                }
                 const int n2 = c3 * (c3 - 1) / 2;
-                const unsigned long long rb = Rhi + (unsigned long long)c3 * (c3 - 1) * (c3 - 2) / 6;
-                if (filt) walk_pairs<W, WP, true>(h2, T, n2, thr, c.base, best, rb);
-                else walk_pairs<W, WP, false>(h2, T, n2, thr, c.base, best, rb);
-            }
-        }
-        // next upper part in colex order: the left-most element that can move up moves,
-        // the ones below it reset (shifted coordinates, bound K')
-        if (on && it + 1 < nup) {
-            int t = 0;
-            while (t < v - 1 && el[t] + 1 >= el[t + 1]) t++;
-            uint32_t rw[W];
-            for (int s = 0; s <= t; s++) {
-                const int col = M + 1 + el[s];
-                rows.load(col, rw);
-#pragma unroll
-                for (int w = 0; w < W; w++) S[w] ^= rw[w];
-                Rhi -= binom_d(c.tb, c.stride, col, P + 2 + s);
-            }
-            el[t] += 1;
-            for (int s = 0; s < t; s++) el[s] = s;
-            for (int s = 0; s <= t; s++) {
-                const int col = M + 1 + el[s];
-                rows.load(col, rw);
-#pragma unroll
-                for (int w = 0; w < W; w++) S[w] ^= rw[w];
-                Rhi += binom_d(c.tb, c.stride, col, P + 2 + s);
+                if (filt) walk_pairs<W, WP, NU, true>(h2, T, n2, thr, c.base, best, rb);
+                else walk_pairs<W, WP, NU, false>(h2, T, n2, thr, c.base, best, rb);
             }
         }
         const int Ug = (int)*(volatile unsigned int *)U;
         Usnap = min(Usnap, Ug);
-        if (best.w < Usnap) {
-            atomicMin(U, (unsigned int)best.w);
-            Usnap = best.w;
+        if (best.w() < Usnap) {
+            atomicMin(U, (unsigned int)best.w());
+            Usnap = best.w();
         }
     }
 }
@@ -304,14 +344,14 @@ __device__ __forceinline__ void simple_chunk(const ChunkCtx &c, unsigned long lo
 #pragma unroll
             for (int w = 0; w < W; w++) acc[w] ^= rw[w];
         }
-        int thr = min(Usnap, best.w - 1) - c.base;
+        // ranks ascend within the lane: a strict improvement keeps the first rank
+        int thr = min(Usnap, best.w()) - c.base;
         for (unsigned long long rank = lo; rank < hi; ++rank) {
             int s = 0;
 #pragma unroll
             for (int w = 0; w < W; w++) s += __popc(acc[w]);
             if (s <= thr) {
-                best.w = s + c.base;
-                best.rank = rank;
+                best.offer(s + c.base, rank);
                 thr = s - 1;
             }
             if (rank + 1 < hi) {
@@ -334,16 +374,15 @@ __device__ __forceinline__ void simple_chunk(const ChunkCtx &c, unsigned long lo
     }
     const int Ug = (int)*(volatile unsigned int *)U;
     Usnap = min(Usnap, Ug);
-    if (best.w < Usnap) {
-        atomicMin(U, (unsigned int)best.w);
-        Usnap = best.w;
+    if (best.w() < Usnap) {
+        atomicMin(U, (unsigned int)best.w());
+        Usnap = best.w();
     }
 }
 
 // Warp min of (weight << 55 | rank) and one atomicMin into the level key.
 __device__ __forceinline__ void publish(unsigned long long *key, const LaneBest &best) {
-    unsigned long long x = best.w < kInf ? (((unsigned long long)best.w << kRankBits) | best.rank) : kNoKey;
-    x = warp_min_u64(x);
+    unsigned long long x = warp_min_u64(best.key);
     if ((threadIdx.x & 31) == 0 && x != kNoKey) atomicMin(key, x);
 }
 

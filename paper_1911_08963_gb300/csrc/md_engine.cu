@@ -65,8 +65,8 @@ __global__ void __launch_bounds__(kEngineThreads) engine_round_kernel(const Engi
         } else {
             const MEntry e = L.mtab[find_entry(L.mtab, L.n_m, item)];
             const GlobSrc<W, WP> h2{L.h2};
-            if (L.kind == KIND_SPLIT2) split_chunk<W, WP, 2>(c, e, item, rows, h2, U, Usnap, best);
-            else split_chunk<W, WP, 3>(c, e, item, rows, h2, U, Usnap, best);
+            if (L.kind == KIND_SPLIT2) split_chunk<W, WP, 2, kNU>(c, e, item, rows, h2, U, Usnap, best);
+            else split_chunk<W, WP, 3, kNU>(c, e, item, rows, h2, U, Usnap, best);
         }
         publish(&cd.keys[cur], best);
     }

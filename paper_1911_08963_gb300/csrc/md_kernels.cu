@@ -66,10 +66,10 @@ __global__ void __launch_bounds__(kThreads, 1) split_kernel(const LevelArgs a) {
         LaneBest best;
         if constexpr (H2S) {
             const SmemSrc<W, WP> h2{sbase + (uint32_t)rows_words * 4u};
-            split_chunk<W, WP, P>(c, e, chunk, rows, h2, &st->U, Usnap, best);
+            split_chunk<W, WP, P, kNU>(c, e, chunk, rows, h2, &st->U, Usnap, best);
         } else {
             const GlobSrc<W, WP> h2{a.h2};
-            split_chunk<W, WP, P>(c, e, chunk, rows, h2, &st->U, Usnap, best);
+            split_chunk<W, WP, P, kNU>(c, e, chunk, rows, h2, &st->U, Usnap, best);
         }
         publish(&st->key[a.level], best);
     }
