@@ -48,6 +48,14 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--verbose", action="store_true", help="per-level records on stderr")
+    ap.add_argument("--batch-count", type=int, default=2048)
+    ap.add_argument("--batch-budget", type=float, default=1e10,
+                    help="batch: per-code work budget in combinations (0 = every code)")
+    ap.add_argument("--serve-count", type=int, default=2000)
+    ap.add_argument("--serve-budget", type=float, default=1e11)
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--profile-once", action="store_true",
+                    help="one md_compute up to --max-stage and exit (a target for ncu captures)")
     return ap.parse_args()
 
 
@@ -112,6 +120,20 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def reduce_over_ranks(seconds: float, codewords: int, device: str):
+    """Replicas: the slowest rank's time and all ranks' codewords (torch.distributed, any
+    backend; a no-op without an initialised process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds, codewords
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(codewords)], dtype=torch.float64, device=device)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(c.item())
 
 
 def measured_peaks():
@@ -235,13 +257,7 @@ def run_ours(args):
     total_s = sum(a.elapsed_time(b) for a, b in ev) * 1e-3
     cw = sum(i["codewords"] for i in infos)
     launches = sum(i["gpu_launches"] for i in infos)
-    if ws > 1:
-        t = torch.tensor([total_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_s = float(t.item())
-        c = torch.tensor([float(cw)], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(c)
-        cw = int(c.item())
+    total_s, cw = reduce_over_ranks(total_s, cw, "cuda")
     value = cw / total_s
 
     # roofline of the dominant kernel: the enumeration kernels of the deepest stage
@@ -330,10 +346,138 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Uneven batch (seed 4): one md_batch schedule vs one md_compute per code, same stream."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1911_08963_gb300 import binding as B
+    from paper_1911_08963_gb300 import inputs
+    codes = inputs.batch_codes(count=args.batch_count)
+    budget = int(args.batch_budget)
+    opt = B.md_options_init(work_budget=budget)
+    opt_loop = B.md_options_init(work_budget=budget, batch_mode=1)
+    B.md_batch(codes[:64], opt)                    # warm-up (module load, first allocations)
+    B.md_batch(codes[:64], opt_loop)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d_b, w_b, st_b = B.md_batch(codes, opt)
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    d_l, w_l, st_l = B.md_batch(codes, opt_loop)
+    t_loop = time.perf_counter() - t0
+    same = d_b == d_l and st_b == st_l and all((x == y).all() for x, y in zip(w_b, w_l))
+    done = sum(1 for s_ in st_b if s_ == B.MD_OK)
+    skipped = sum(1 for s_ in st_b if s_ == B.MD_EBUDGET)
+    hist = {}
+    for (G, n, k), s_ in zip(codes, st_b):
+        key = "n%d-%d" % (n // 25 * 25, n // 25 * 25 + 24)
+        h = hist.setdefault(key, [0, 0])
+        h[0 if s_ == B.MD_OK else 1] += 1
+    line = {"metric": "codes/s (batched vs per-code loop)", "value": done / t_batch, "unit": "codes/s",
+            "per_code_loop": done / t_loop, "speedup": t_loop / t_batch, "codes": len(codes), "completed": done,
+            "skipped_over_budget": skipped, "seconds_batched": t_batch, "seconds_loop": t_loop,
+            "identical_results": same, "higher_is_better": True, "n_gpus": 1,
+            "config": {"workload": "2048 random codes, seed 4, n~U{48..160}, k~U{n/3..n/2}",
+                       "work_budget": budget, "histogram_done_skipped_by_n": hist}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Poisson stream (seed 5, 200 requests/s) through the continuous-batching server."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1911_08963_gb300 import binding as B
+    from paper_1911_08963_gb300 import inputs
+    trace = inputs.serving_trace(args.serve_count)
+    s = B.md_server_create(slots=args.serve_slots, work_budget=int(args.serve_budget))
+    # warm-up: a few small codes through the server
+    for t, G, n, k in trace[:8]:
+        try:
+            tk = B.md_server_submit(s, G, n, k)
+            while B.md_server_poll(s, tk, n) is None:
+                time.sleep(0.0005)
+        except B.MDError:
+            pass
+    outstanding = {}
+    lat = []
+    rejected = 0
+    lock = threading.Lock()
+    start = time.perf_counter()
+    stop = [False]
+
+    def poller():
+        while not stop[0] or outstanding:
+            with lock:
+                items = list(outstanding.items())
+            for tk, (arr, n) in items:
+                r = B.md_server_poll(s, tk, n)
+                if r is not None:
+                    now = time.perf_counter() - start
+                    with lock:
+                        del outstanding[tk]
+                        lat.append((now - arr, r[2]))
+            time.sleep(0.0002)
+
+    th = threading.Thread(target=poller)
+    th.start()
+    for arr, G, n, k in trace:
+        delay = arr - (time.perf_counter() - start)
+        if delay > 0:
+            time.sleep(delay)
+        try:
+            tk = B.md_server_submit(s, G, n, k)
+            with lock:
+                outstanding[tk] = (arr, n)
+        except B.MDError as e:
+            if e.code != B.MD_EBUDGET:
+                raise
+            rejected += 1
+    stop[0] = True
+    th.join()
+    makespan = time.perf_counter() - start
+    B.md_server_destroy(s)
+    ok = sorted(x for x, st in lat if st == B.MD_OK)
+    p = lambda q: ok[min(len(ok) - 1, int(q * len(ok)))] if ok else None
+    line = {"metric": "serving latency p50/p99 and codes/s", "value": len(ok) / makespan, "unit": "codes/s",
+            "p50_ms": p(0.50) * 1e3 if ok else None, "p99_ms": p(0.99) * 1e3 if ok else None,
+            "completed": len(ok), "rejected_over_budget": rejected, "requests": len(trace),
+            "makespan_s": makespan, "trace_s": trace[-1][0], "higher_is_better": True, "n_gpus": 1,
+            "config": {"workload": "Poisson arrivals 200/s, seed 5, n~U{64..200}, k=n/2+U{-8..8}",
+                       "work_budget": int(args.serve_budget), "slots": args.serve_slots}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_profile_once(args):
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1911_08963_gb300 import binding as B
+    from paper_1911_08963_gb300 import inputs
+    G, n, k = inputs.single_code(args.workload)
+    h = B.md_create(G, n, k, B.md_options_init(max_stage=args.max_stage, filter=args.filter))
+    d, _ = B.md_compute(h, n)
+    info = B.md_info_get(h)
+    B.md_destroy(h)
+    print(json.dumps({"workload": args.workload, "max_stage": args.max_stage, "d": d,
+                      "codewords": info["codewords"], "seconds_device": info["seconds_device"]}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_once:
+        return run_profile_once(args)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -71,8 +71,11 @@ typedef struct md_options {
     int threads_per_block;    /* 0 = default (512) */
     int blocks_per_sm;        /* 0 = default (occupancy-derived) */
     int filter;               /* 1 (default) = reject codewords with a one-popcount lower
-                                 bound when it proves wt > U; 0 = exact weight of every
-                                 codeword; 2 = always filter */
+                                 bound (popcount of the OR of the fewest packed words that
+                                 still proves wt > U for almost all of them); 0 = exact
+                                 weight of every codeword; 2 = also filter with all words
+                                 when no word count qualifies; 3 = always filter with one
+                                 word (a test setting).  Results are identical for all. */
     void *stream;             /* cudaStream_t to run on; NULL = the library's own stream */
     volatile int *cancel_flag;/* optional host flag (pinned or ordinary memory): set non-zero
                                  to cancel; polled between stages */

@@ -209,7 +209,7 @@ LevelArgs level_args(md_ctx *h, const LevelPlan &p, int level, bool h2s) {
     a.v = p.v;
     a.base = p.base;
     a.level = level;
-    a.filter_max = p.filter_max;
+    a.fmax8 = p.fmax8;
     a.h2_in_smem = h2s ? 1 : 0;
     a.m_total = (int)h->code.gam.size();
     a.j = p.j;

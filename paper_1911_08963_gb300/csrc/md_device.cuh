@@ -22,10 +22,7 @@ namespace dev {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kInf = 0x3fffffff;
-#ifndef MD_UPPERS_PER_LANE
-#define MD_UPPERS_PER_LANE 2
-#endif
-constexpr int kNU = MD_UPPERS_PER_LANE;       // upper parts a lane walks against each loaded head
+constexpr int kNU = kUppersPerLane;           // upper parts a lane walks against each loaded head
 
 __device__ __forceinline__ unsigned long long binom_d(const unsigned long long *tb, int stride, int a, int b) {
     return (b < 0 || b > a) ? 0ull : __ldg(tb + (size_t)a * stride + b);
@@ -99,13 +96,27 @@ __device__ __forceinline__ int weight_xor(const uint32_t (&T)[W], const uint32_t
     return s;
 }
 
-// Lower bound of the weight: popc of the OR of the words (one POPC for all W words).
-template <int W>
-__device__ __forceinline__ int weight_lb_or(const uint32_t (&T)[W], const uint32_t (&h)[W]) {
-    uint32_t o = T[0] ^ h[0];
+// Lower bound of the weight: popc of the OR of the first F words (one POPC for F words;
+// F = 0 means the exact weight).  Each bit position is counted at most once, so the bound
+// never exceeds the weight.
+template <int W, int F>
+__device__ __forceinline__ int weight_lb(const uint32_t (&T)[W], const uint32_t (&h)[W]) {
+    if constexpr (F == 0) {
+        return weight_xor<W>(T, h);
+    } else {
+        uint32_t o = T[0] ^ h[0];
 #pragma unroll
-    for (int w = 1; w < W; w++) o |= T[w] ^ h[w];
-    return __popc(o);
+        for (int w = 1; w < F; w++) o |= T[w] ^ h[w];
+        return __popc(o);
+    }
+}
+
+__device__ __forceinline__ int min3(int a, int b, int c) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    return __vimin3_s32(a, b, c);
+#else
+    return min(min(a, b), c);
+#endif
 }
 
 __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long x) {
@@ -133,7 +144,7 @@ struct LaneBest {
 // exact weights of codewords that pass are offered to the lane's best with their ranks
 // rbase[q] + i.  One loaded entry serves all NU sums (the unrolling of the paper's
 // saved-additions engine, Section 2.2.1: several left combinations share each right one).
-template <int W, int WP, int NU, bool FILTER, class H2Src>
+template <int W, int WP, int NU, int F, class H2Src>
 __device__ __forceinline__ void walk_pairs(const H2Src &h2, const uint32_t (&T)[NU][W], int n2, int &thr, int base,
                                            LaneBest &best, const unsigned long long (&rbase)[NU]) {
     int i = 0;
@@ -143,10 +154,11 @@ __device__ __forceinline__ void walk_pairs(const H2Src &h2, const uint32_t (&T)[
         for (int u = 0; u < 8; u++) {
             uint32_t h[W];
             h2.load(i + u, h);
+            if constexpr (NU == 2) {
+                lbmin = min3(lbmin, weight_lb<W, F>(T[0], h), weight_lb<W, F>(T[1], h));
+            } else {
 #pragma unroll
-            for (int q = 0; q < NU; q++) {
-                const int lb = FILTER ? weight_lb_or<W>(T[q], h) : weight_xor<W>(T[q], h);
-                lbmin = min(lbmin, lb);
+                for (int q = 0; q < NU; q++) lbmin = min(lbmin, weight_lb<W, F>(T[q], h));
             }
         }
         if (__any_sync(kFull, lbmin <= thr)) {
@@ -178,9 +190,27 @@ __device__ __forceinline__ void walk_pairs(const H2Src &h2, const uint32_t (&T)[
     }
 }
 
+// Run walk_pairs with F filter words (runtime value, 0..W).
+template <int W, int WP, int NU, class H2Src>
+__device__ __forceinline__ void walk_dispatch(int F, const H2Src &h2, const uint32_t (&T)[NU][W], int n2, int &thr,
+                                              int base, LaneBest &best, const unsigned long long (&rbase)[NU]) {
+    switch (F) {
+        case 1: walk_pairs<W, WP, NU, 1>(h2, T, n2, thr, base, best, rbase); break;
+        case 2: if constexpr (W >= 2) walk_pairs<W, WP, NU, 2>(h2, T, n2, thr, base, best, rbase); break;
+        case 3: if constexpr (W >= 3) walk_pairs<W, WP, NU, 3>(h2, T, n2, thr, base, best, rbase); break;
+        case 4: if constexpr (W >= 4) walk_pairs<W, WP, NU, 4>(h2, T, n2, thr, base, best, rbase); break;
+        case 5: if constexpr (W >= 5) walk_pairs<W, WP, NU, 5>(h2, T, n2, thr, base, best, rbase); break;
+        case 6: if constexpr (W >= 6) walk_pairs<W, WP, NU, 6>(h2, T, n2, thr, base, best, rbase); break;
+        case 7: if constexpr (W >= 7) walk_pairs<W, WP, NU, 7>(h2, T, n2, thr, base, best, rbase); break;
+        case 8: if constexpr (W >= 8) walk_pairs<W, WP, NU, 8>(h2, T, n2, thr, base, best, rbase); break;
+        default: walk_pairs<W, WP, NU, 0>(h2, T, n2, thr, base, best, rbase); break;
+    }
+}
+
 // Level-constant parameters of a chunk.
 struct ChunkCtx {
-    int k, g, v, base, filter_max;
+    int k, g, v, base;
+    unsigned long long fmax8;      // byte f-1: 1 + largest threshold for an f-word filter
     const unsigned long long *tb;
     int stride;
 };
@@ -285,11 +315,16 @@ __device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, 
             }
         }
         int thr = on ? min(Usnap, best.w()) - c.base : -1;
-        const bool filt = __all_sync(kFull, thr <= c.filter_max);
+        // filter words: the fewest whose popcount-of-OR bound still rejects almost every
+        // codeword at the warp's largest threshold (0 = exact weights)
+        const int tmax = __reduce_max_sync(kFull, thr);
+        int F = 0;
+#pragma unroll
+        for (int f = W; f >= 1; f--)
+            if (tmax < (int)((c.fmax8 >> (8 * (f - 1))) & 0xff)) F = f;
         if constexpr (P == 2) {
             const int n2 = M * (M - 1) / 2;
-            if (filt) walk_pairs<W, WP, NU, true>(h2, S, n2, thr, c.base, best, R);
-            else walk_pairs<W, WP, NU, false>(h2, S, n2, thr, c.base, best, R);
+            walk_dispatch<W, WP, NU>(F, h2, S, n2, thr, c.base, best, R);
         } else {
             for (int c3 = 2; c3 < M; c3++) {
                 uint32_t T[NU][W], rw[W];
@@ -303,8 +338,7 @@ __device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, 
                     rb[q] = R[q] + h3;
                 }
                 const int n2 = c3 * (c3 - 1) / 2;
-                if (filt) walk_pairs<W, WP, NU, true>(h2, T, n2, thr, c.base, best, rb);
-                else walk_pairs<W, WP, NU, false>(h2, T, n2, thr, c.base, best, rb);
+                walk_dispatch<W, WP, NU>(F, h2, T, n2, thr, c.base, best, rb);
             }
         }
         const int Ug = (int)*(volatile unsigned int *)U;

@@ -133,7 +133,7 @@ int Engine::fill_code(PreparedCode &pc, char *header, char *h2, std::vector<char
         L.v = p.v;
         L.base = p.base;
         L.kind = p.kind;
-        L.filter_max = p.filter_max;
+        L.fmax8 = p.fmax8;
         L.L_after = p.L_after;
         L.j = p.j;
         L.W = cd.gam[p.j].W;

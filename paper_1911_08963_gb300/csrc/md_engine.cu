@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kEngineThreads) engine_round_kernel(const Engi
         const unsigned long long item = *(volatile const unsigned long long *)&stv.next_item + ticket -
                                         (lo ? __ldg(prefix + lo - 1) : 0ull);
         const BLevel L = cd.levels[cur];
-        const ChunkCtx c{cd.k, L.g, L.v, L.base, L.filter_max, a.binom, kBinomStride};
+        const ChunkCtx c{cd.k, L.g, L.v, L.base, L.fmax8, a.binom, kBinomStride};
         unsigned int *U = &a.states[slot].U;
         int Usnap = (int)*(volatile unsigned int *)U;
         const GlobSrc<W, WP> rows{L.rows};

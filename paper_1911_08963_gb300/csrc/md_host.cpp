@@ -261,13 +261,13 @@ double estimate_work(const Code &c, int *d_est, int *g_stop) {
     return work;
 }
 
-int filter_threshold(const Gamma &gm) {
+int filter_threshold(const Gamma &gm, int f) {
     const int bits = (int)gm.packed_cols.size();
-    // per bit position b of a 32-bit word: how many packed words have a column there
+    // per bit position b of a 32-bit word: how many of the first f words have a column there
     double dist[33] = {1.0};
     for (int b = 0; b < 32; b++) {
         int nb = 0;
-        for (int w = 0; w < gm.W; w++)
+        for (int w = 0; w < f && w < gm.W; w++)
             if (32 * w + b < bits) nb++;
         double p = nb ? 1.0 - std::ldexp(1.0, -nb) : 0.0;
         for (int t = b + 1; t >= 1; t--) dist[t] = dist[t] * (1 - p) + dist[t - 1] * p;
@@ -282,6 +282,22 @@ int filter_threshold(const Gamma &gm) {
     return best;
 }
 
+// mode 0: never filter; 1: every word count whose threshold allows it; 2: also always with
+// all words; 3: always with one word (a test setting that sends many codewords down the
+// exact path).
+unsigned long long filter_thresholds(const Gamma &gm, int mode) {
+    unsigned long long out = 0;
+    if (mode == 0) return 0;
+    for (int f = 1; f <= gm.W && f <= 8; f++) {
+        int t = filter_threshold(gm, f);
+        if (mode == 2 && f == gm.W) t = 254;
+        if (mode == 3) t = (f == 1) ? 254 : -1;
+        const unsigned long long byte = (unsigned long long)(t < 0 ? 0 : std::min(255, t + 1));
+        out |= byte << (8 * (f - 1));
+    }
+    return out;
+}
+
 LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o) {
     LevelPlan p;
     const Gamma &gm = c.gam[j];
@@ -290,7 +306,7 @@ LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o) {
     p.count = binom(k, g);
     p.base = gm.weight_base_is_g ? g : 0;
     p.L_after = lower_bound_after(c, g);
-    p.filter_max = o.filter == 0 ? -1 : o.filter == 2 ? 1 << 20 : filter_threshold(gm);
+    p.fmax8 = filter_thresholds(gm, o.filter);
     const uint64_t target_full = 1ull << std::max(8, std::min(30, o.chunk_log2));
     // keep at least ~64 work items per SM-sized slice of the level
     const uint64_t target = std::max<uint64_t>(1ull << 10, std::min<uint64_t>(target_full, p.count / (152ull * 64)));
@@ -313,6 +329,8 @@ LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o) {
         per_lane = std::max<uint64_t>(1, std::min<uint64_t>(per_lane, 1u << 30));
         const uint64_t need = (e.uppers + 31) / 32;       // never more than the lanes can use
         per_lane = std::min(per_lane, std::max<uint64_t>(1, need));
+        // lanes walk kUppersPerLane upper parts at once: whole groups avoid repeated work
+        per_lane = (per_lane + kUppersPerLane - 1) / kUppersPerLane * kUppersPerLane;
         e.per_lane = (uint32_t)per_lane;
         e.chunk_begin = chunks;
         chunks += (e.uppers + 32 * per_lane - 1) / (32 * per_lane);

@@ -12,6 +12,10 @@ namespace mdl {
 constexpr int kMaxN = MD_MAX_N;
 constexpr int kMaxWords = kMaxN / 32;         // 32-bit words of a packed row
 constexpr int kMaxG = 64;                     // deepest stage g handled
+#ifndef MD_UPPERS_PER_LANE
+#define MD_UPPERS_PER_LANE 2
+#endif
+constexpr int kUppersPerLane = MD_UPPERS_PER_LANE;  // upper parts a lane walks at once
 constexpr int kMaxLevels = MD_MAX_LEVELS;
 constexpr int kRankBits = 55;                 // level key = weight << 55 | colex rank
 constexpr uint64_t kRankLimit = 1ull << kRankBits;
@@ -71,7 +75,9 @@ struct LevelPlan {
     int v = 0;                      // upper elements per lane (kinds 2, 3)
     int base = 0;                   // weight base (g or 0)
     int L_after = 0;                // lower bound after this stage (used when j = m - 1)
-    int filter_max = -1;            // largest threshold at which the popcount-of-OR filter pays
+    // filter thresholds: byte f-1 holds 1 + the largest packed-weight threshold at which the
+    // popcount of the OR of the first f words still rejects almost every codeword (0 = never)
+    unsigned long long fmax8 = 0;
     uint64_t count = 0;             // C(k, g)
     uint64_t nchunks = 0;
     uint64_t per_chunk = 0;         // kind 0: ranks per lane
@@ -85,9 +91,10 @@ struct PlanOptions {
 
 LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o);
 
-// Largest threshold t with P(popcount(OR of the packed words) <= t) below 1e-5 for
-// uniformly random packed rows: above it the filter would rarely reject.
-int filter_threshold(const Gamma &gm);
+// Largest threshold t with P(popcount(OR of the first f packed words) <= t) below 1e-5 for
+// uniformly random packed rows (-1 if none): above it the filter would rarely reject.
+int filter_threshold(const Gamma &gm, int f);
+unsigned long long filter_thresholds(const Gamma &gm, int mode);
 
 // -------------------------------------------------------------------- device side ---
 
@@ -117,7 +124,7 @@ struct LevelArgs {
     unsigned long long per_chunk;
     int n_m;
     int k, g, v, base, level;
-    int filter_max;
+    unsigned long long fmax8;
     int h2_in_smem;
     int m_total;                    // number of Gamma matrices
     int j;
@@ -134,7 +141,8 @@ struct BLevel {
     const uint32_t *h2;             // Gamma_j pair table
     const MEntry *mtab;
     unsigned long long nchunks, count, per_chunk;
-    int n_m, g, v, base, kind, filter_max, L_after, j, W, WP, pad0, pad1;
+    unsigned long long fmax8;
+    int n_m, g, v, base, kind, L_after, j, W, WP, pad0;
 };
 
 // A slot of the engine: one resident code (written by the host on admission).

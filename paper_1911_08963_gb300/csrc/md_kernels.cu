@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_kernel(const LevelArgs a) {
 
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const SmemSrc<W, WP> rows{sbase};
-    const ChunkCtx c{k, a.g, a.v, a.base, a.filter_max, a.binom, k + 1};
+    const ChunkCtx c{k, a.g, a.v, a.base, a.fmax8, a.binom, k + 1};
     const int lane = threadIdx.x & 31;
     int Usnap = (int)*(volatile unsigned int *)&st->U;
 
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kThreads, 1) simple_kernel(const LevelArgs a) 
     stage_to_smem(smem, a.rows, k * WP);
     __syncthreads();
     const SmemSrc<W, WP> rows{(uint32_t)__cvta_generic_to_shared(smem)};
-    const ChunkCtx c{k, a.g, a.v, a.base, a.filter_max, a.binom, k + 1};
+    const ChunkCtx c{k, a.g, a.v, a.base, a.fmax8, a.binom, k + 1};
     const int lane = threadIdx.x & 31;
     int Usnap = (int)*(volatile unsigned int *)&st->U;
     for (;;) {

@@ -86,7 +86,7 @@ def oracle_bz_cached(G, n, k, key):
 
 
 @pytest.mark.parametrize("n,k,seed", RANDOM_CASES)
-@pytest.mark.parametrize("filt", [0, 1, 2])
+@pytest.mark.parametrize("filt", [0, 1, 2, 3])
 def test_random_codes(B, n, k, seed, filt):
     rows = T.random_rows(n, k, seed)
     G = T.pack(rows, n)
