@@ -4,9 +4,11 @@
 One step = md_compute on G = [I_100 | R] (R from SplitMix64 seed 3, the first invertible
 draw) running every level of stages g = 1..--max-stage (default 10) to completion: both
 Gamma matrices, every g-row combination, ~3.9e13 codewords at g <= 10.  The metric is
-codewords/s = the sum of C(k, g) over the completed levels / device time.
+codewords/s = the sum of C(k, g) over the completed levels / device time.  At N = 1 the
+full computation to d (time-to-d, ~3.2e14 codewords) also runs once, after the timed steps.
 
-    python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--time-to-d]
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-time-to-d]
+    python bench.py --workload batch | --workload serve     (the batched and serving workloads)
 
 Under torchrun (N > 1) every rank runs an independent replica of the step on its own GPU
 (the path has no cross-GPU exchange); value = all ranks' codewords / the slowest rank's
@@ -32,6 +34,9 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 POPC_PER_SM_PER_CLK = 16          # measured on GB300 (popc.b32 throughput per SM per clock)
 NOMINAL_SMS = 152
 NOMINAL_MAX_MHZ = 2070.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one split_kernel launch (level g=8 of
+# rand200x100) measured with ncu on the current kernel; to be re-measured when it changes
+SPLIT_KERNEL_TRAFFIC_BYTES = 160256 + 700928
 
 
 def parse():
@@ -43,12 +48,14 @@ def parse():
     ap.add_argument("--workload", default="rand200x100")
     ap.add_argument("--max-stage", type=int, default=10)
     ap.add_argument("--filter", type=int, default=1)
-    ap.add_argument("--time-to-d", action="store_true", help="also run the full computation once (time-to-d)")
+    ap.add_argument("--no-time-to-d", action="store_true",
+                    help="skip the full computation to d (run once on rank 0 at N=1 by default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--verbose", action="store_true", help="per-level records on stderr")
     ap.add_argument("--batch-count", type=int, default=2048)
+    ap.add_argument("--chunk-log2", type=int, default=0, help="log2 combinations per work item (0 = library default)")
     ap.add_argument("--batch-budget", type=float, default=1e10,
                     help="batch: per-code work budget in combinations (0 = every code)")
     ap.add_argument("--serve-count", type=int, default=2000)
@@ -270,7 +277,9 @@ def run_ours(args):
     peak = POPC_PER_SM_PER_CLK * NOMINAL_SMS * NOMINAL_MAX_MHZ * 1e6 / 1e9       # Gpopc/s
     achieved = per_launch_cw * 1.0 / per_launch_s / 1e9                              # 1 popc per codeword (filtered)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpopc/s", "frac": achieved / peak,
-                "traffic": None,
+                "traffic": SPLIT_KERNEL_TRAFFIC_BYTES,
+                "traffic_note": "dram read+write per launch, ncu on the same kernel (level g=8 launch); "
+                                "fixed staging cost, does not grow with codewords",
                 "kernel": "split_kernel (stage g=%d levels, %d launches timed)" % (top_g, len(top)),
                 "peak_basis": "16 popc/clk/SM (measured) x 152 SMs x 2070 MHz max clock",
                 "work_basis": "1 popc per codeword: popcount of the OR of the packed words, exact weight "
@@ -293,9 +302,6 @@ def run_ours(args):
     if rank == 0 and not args.no_e2e:
         # end to end through the C ABI from host buffers: create (host G), compute, destroy
         opt_e = B.md_options_init(max_stage=args.max_stage, filter=args.filter)
-        hh = B.md_create(G, n, k, opt_e)
-        B.md_compute(hh, n)
-        B.md_destroy(hh)
         times, h2d, d2h, cwe = [], 0, 0, 0
         for _ in range(args.steps):
             t0 = time.perf_counter()
@@ -317,7 +323,7 @@ def run_ours(args):
                                 "sample": "colex-rank prefix of level (g=%d, Gamma_1): %d combinations, %.1f s"
                                           % (args.max_stage, size, dt)}
 
-    if rank == 0 and args.time_to_d:
+    if rank == 0 and ws == 1 and not args.no_time_to_d and args.workload == "rand200x100":
         opt_f = B.md_options_init(filter=args.filter, stream=stream.cuda_stream)
         hf = B.md_create(G, n, k, opt_f)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -356,8 +362,8 @@ def run_batch(args):
     from paper_1911_08963_gb300 import inputs
     codes = inputs.batch_codes(count=args.batch_count)
     budget = int(args.batch_budget)
-    opt = B.md_options_init(work_budget=budget)
-    opt_loop = B.md_options_init(work_budget=budget, batch_mode=1)
+    opt = B.md_options_init(work_budget=budget, chunk_log2=args.chunk_log2)
+    opt_loop = B.md_options_init(work_budget=budget, batch_mode=1, chunk_log2=args.chunk_log2)
     B.md_batch(codes[:64], opt)                    # warm-up (module load, first allocations)
     B.md_batch(codes[:64], opt_loop)
     torch.cuda.synchronize()

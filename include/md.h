@@ -83,6 +83,9 @@ typedef struct md_options {
                                  round schedule; 1 = one md_compute per code, in order */
     int use_graph;            /* md_batch only: 1 (default) = capture the round schedule in a
                                  CUDA graph and launch it once; 0 = plain stream launches */
+    int plan_horizon;         /* md_batch only: stages planned past each code's estimated
+                                 stopping stage (0 = default 3); a code that needs more is
+                                 finished by a single-code run, with the same result */
 } md_options;
 
 /* Result details of the last md_compute on a handle. */

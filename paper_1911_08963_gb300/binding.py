@@ -29,7 +29,7 @@ class md_options(ctypes.Structure):
     _fields_ = [("work_budget", ctypes.c_uint64), ("max_stage", ctypes.c_int), ("chunk_log2", ctypes.c_int),
                 ("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("filter", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("cancel_flag", ctypes.POINTER(ctypes.c_int)),
-                ("batch_mode", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("batch_mode", ctypes.c_int), ("use_graph", ctypes.c_int), ("plan_horizon", ctypes.c_int)]
 
 
 class md_info(ctypes.Structure):

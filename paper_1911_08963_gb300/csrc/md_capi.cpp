@@ -43,6 +43,11 @@ struct md_ctx {
     std::vector<size_t> mtab_offset;        // per level, entries into dev.mtab
     int g_limit = 0;                        // deepest stage that can be planned
     DevState *host_state = nullptr;         // pinned copy of the device state
+    struct Head { unsigned int U; int L, stop, error, last_level; };
+    Head *heads = nullptr;                  // pinned, one per stage: the stop flag a stage behind
+    std::vector<cudaEvent_t> lev_ev;        // timing events, two per level
+    std::vector<cudaEvent_t> stage_ev;      // one per stage
+    cudaEvent_t run_ev[2] = {nullptr, nullptr};
     md_info info{};
     std::vector<md_level> levels;
     int threads = kDefaultThreads;
@@ -72,6 +77,14 @@ void free_device(md_ctx *h) {
     h->dev = DevLayout();
     if (h->host_state) cudaFreeHost(h->host_state);
     h->host_state = nullptr;
+    if (h->heads) cudaFreeHost(h->heads);
+    h->heads = nullptr;
+    for (cudaEvent_t e : h->lev_ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->stage_ev) cudaEventDestroy(e);
+    h->lev_ev.clear();
+    h->stage_ev.clear();
+    for (cudaEvent_t &e : h->run_ev)
+        if (e) { cudaEventDestroy(e); e = nullptr; }
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     h->own_stream = nullptr;
     h->dev_ready = false;
@@ -130,7 +143,19 @@ int setup_device(md_ctx *h) {
     off = align256(off + sizeof(DevState));
 
     if (cudaMalloc(&h->dev.base, off) != cudaSuccess) { cudaGetLastError(); free_device(h); return MD_ENOMEM; }
-    if (cudaMallocHost(&h->host_state, sizeof(DevState)) != cudaSuccess) { cudaGetLastError(); free_device(h); return MD_ENOMEM; }
+    if (cudaMallocHost(&h->host_state, sizeof(DevState)) != cudaSuccess ||
+        cudaMallocHost(&h->heads, sizeof(md_ctx::Head) * std::max(1, h->g_limit)) != cudaSuccess) {
+        cudaGetLastError();
+        free_device(h);
+        return MD_ENOMEM;
+    }
+    // events reused by every md_compute on this handle
+    h->lev_ev.resize((size_t)2 * h->g_limit * m);
+    h->stage_ev.resize(h->g_limit);
+    for (cudaEvent_t &e : h->lev_ev) cudaEventCreate(&e);
+    for (cudaEvent_t &e : h->stage_ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    cudaEventCreate(&h->run_ev[0]);
+    cudaEventCreate(&h->run_ev[1]);
     h->dev.bytes = off;
     h->dev.rows.resize(m);
     h->dev.h2.resize(m);
@@ -306,12 +331,9 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
     fill_static_info(h);
     h->levels.clear();
 
-    cudaEvent_t ev0, ev1;
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
-    // one pinned slot per stage for the stop flag (first 32 bytes of the state)
-    std::vector<cudaEvent_t> stage_ev;
-    std::vector<cudaEvent_t> lev_ev;            // before/after each level's kernel
+    cudaEvent_t ev0 = h->run_ev[0], ev1 = h->run_ev[1];
+    using Head = md_ctx::Head;
+    int nlev_ev = 0, nstages = 0;
     int launches = 0;
     uint64_t h2d = 0, d2h = 0;
     bool err = launch_state_init(h->dev.st, (unsigned)(n + 1), s) != 0;
@@ -319,8 +341,6 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
     cudaEventRecord(ev0, s);
     uint64_t planned = 0;
     int status = MD_OK;
-    struct Head { unsigned int U; int L, stop, error, last_level; };
-    std::vector<Head *> heads;
     bool stopped = false;
     int g = 1;
     for (; g <= k && !err; g++) {
@@ -344,46 +364,33 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
             const LevelPlan &p = h->plans[level];
             LaunchCfg L = launch_cfg(h, p);
             LevelArgs a = level_args(h, p, level, L.h2s);
-            cudaEvent_t e0, e1;
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            cudaEventRecord(e0, s);
+            cudaEventRecord(h->lev_ev[nlev_ev], s);
             err |= launch_level(a, p.kind, c.gam[p.j].W, c.gam[p.j].WP, L.blocks, L.threads, L.smem, s) != 0;
-            cudaEventRecord(e1, s);
-            lev_ev.push_back(e0);
-            lev_ev.push_back(e1);
+            cudaEventRecord(h->lev_ev[nlev_ev + 1], s);
+            nlev_ev += 2;
             err |= launch_finalize(a, s) != 0;
             launches += 2;
         }
-        Head *hd = nullptr;
-        if (cudaMallocHost(&hd, sizeof(Head)) != cudaSuccess) { err = true; break; }
-        heads.push_back(hd);
+        Head *hd = h->heads + nstages;
         cudaMemcpyAsync(hd, h->dev.st, sizeof(Head), cudaMemcpyDeviceToHost, s);
         d2h += sizeof(Head);
-        cudaEvent_t e;
-        cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-        cudaEventRecord(e, s);
-        stage_ev.push_back(e);
+        cudaEventRecord(h->stage_ev[nstages], s);
+        nstages++;
         // look one stage behind: the device keeps working on the stage just queued
-        if (stage_ev.size() >= 2) {
-            cudaEventSynchronize(stage_ev[stage_ev.size() - 2]);
-            if (heads[heads.size() - 2]->stop) { stopped = true; break; }
+        if (nstages >= 2) {
+            cudaEventSynchronize(h->stage_ev[nstages - 2]);
+            if (h->heads[nstages - 2].stop) { stopped = true; break; }
         }
     }
     cudaEventRecord(ev1, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) err = true;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
-    std::vector<double> lev_sec(lev_ev.size() / 2, 0.0);
-    for (size_t i = 0; i + 1 < lev_ev.size(); i += 2) {
+    std::vector<double> lev_sec(nlev_ev / 2, 0.0);
+    for (int i = 0; i + 1 < nlev_ev; i += 2) {
         float lms = 0.f;
-        if (cudaEventElapsedTime(&lms, lev_ev[i], lev_ev[i + 1]) == cudaSuccess) lev_sec[i / 2] = lms * 1e-3;
+        if (cudaEventElapsedTime(&lms, h->lev_ev[i], h->lev_ev[i + 1]) == cudaSuccess) lev_sec[i / 2] = lms * 1e-3;
     }
-    for (auto e : lev_ev) cudaEventDestroy(e);
-    for (auto e : stage_ev) cudaEventDestroy(e);
-    for (auto p : heads) cudaFreeHost(p);
-    cudaEventDestroy(ev0);
-    cudaEventDestroy(ev1);
     if (err) { cudaGetLastError(); return MD_ECUDA; }
     if (cudaMemcpy(h->host_state, h->dev.st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) return MD_ECUDA;
     d2h += sizeof(DevState);

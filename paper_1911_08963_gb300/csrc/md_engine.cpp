@@ -2,7 +2,9 @@
 #include "md_engine.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
+#include <thread>
 
 namespace mdl {
 
@@ -14,18 +16,23 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
 int prepare_code(const uint64_t *G, int n, int k, const PlanOptions &po, int max_stage, uint64_t budget,
-                 PreparedCode *out) {
+                 PreparedCode *out, int horizon) {
     PreparedCode p;
     int rc = build_code(G, n, k, &p.code);
     if (rc != MD_OK) return rc;
-    if (budget && estimate_work(p.code, nullptr, nullptr) > (double)budget) return MD_EBUDGET;
+    int g_est = 0;
+    const double work = estimate_work(p.code, nullptr, &g_est);
+    if (budget && work > (double)budget) return MD_EBUDGET;
     const int m = (int)p.code.gam.size();
     for (int g = 1; g <= std::min(k, kMaxG); g++) {
         if (binom(k, g) >= kRankLimit) break;
         if (max_stage > 0 && g > max_stage) break;
         if ((size_t)g * m > (size_t)kMaxLevels) break;
-        p.g_limit = g;
+        p.g_max = g;
     }
+    // plans (and their device tables) only a few stages past the estimated stop; a code
+    // that runs past them is finished by a single-code run
+    p.g_limit = horizon > 0 ? std::min(p.g_max, g_est + horizon) : p.g_max;
     p.max_stage = max_stage;
     size_t nm = 0;
     for (int g = 1; g <= p.g_limit; g++)
@@ -45,6 +52,24 @@ int prepare_code(const uint64_t *G, int n, int k, const PlanOptions &po, int max
     p.h2_bytes = h2;
     *out = std::move(p);
     return MD_OK;
+}
+
+void prepare_codes(const md_code *codes, int count, const PlanOptions &po, int max_stage, uint64_t budget,
+                   std::vector<PreparedCode> &out, int *status, int horizon) {
+    out.resize(count);
+    const int nt = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), std::min(32, count / 8 + 1)));
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= count) break;
+            status[i] = prepare_code(codes[i].G, codes[i].n, codes[i].k, po, max_stage, budget, &out[i], horizon);
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 1; t < nt; t++) th.emplace_back(work);
+    work();
+    for (auto &t : th) t.join();
 }
 
 Engine::~Engine() { release_all(); }
@@ -84,7 +109,7 @@ int Engine::init(int nslots, cudaStream_t stream, unsigned long long quota, int 
     args_.act_total = (unsigned long long *)(tables_ + tot_off);
     args_.tick_ctr = (unsigned long long *)(tables_ + ctr_off);
     args_.binom = (const unsigned long long *)(tables_ + bin_off);
-    args_.quota = quota;
+    quota_cw_ = quota;
     for (int w = 1; w < kWClasses; w++) {
         int per = engine_blocks_per_sm(w, kThreads);
         if (cap_ > 0) per = std::min(std::max(1, per), cap_);
@@ -134,6 +159,10 @@ int Engine::fill_code(PreparedCode &pc, char *header, char *h2, std::vector<char
         L.base = p.base;
         L.kind = p.kind;
         L.fmax8 = p.fmax8;
+        if (quota_cw_ && p.nchunks) {
+            const unsigned long long per_item = std::max<unsigned long long>(1, p.count / p.nchunks);
+            L.quota = std::max<unsigned long long>(1, quota_cw_ / per_item);
+        }
         L.L_after = p.L_after;
         L.j = p.j;
         L.W = cd.gam[p.j].W;
@@ -330,9 +359,11 @@ int Engine::collect(int slot, const PreparedCode &pc, const BState &st, CodeResu
     if (popcount_row(res->witness.data(), cd.nw64) != U) { res->status = MD_EINTERNAL; return MD_OK; }
     res->d = U;
     res->status = MD_OK;
-    if (!res->complete)
-        res->status = (pc.g_limit < cd.k && (pc.max_stage <= 0 || pc.g_limit < pc.max_stage)) ? MD_EUNSUPPORTED
-                                                                                           : MD_EBUDGET;
+    if (!res->complete) {
+        if (pc.g_limit < pc.g_max) res->status = MD_EAGAIN_INTERNAL;      // ran past the planned stages
+        else if (pc.max_stage > 0 && pc.g_limit >= pc.max_stage) res->status = MD_EBUDGET;
+        else res->status = MD_EUNSUPPORTED;
+    }
     return MD_OK;
 }
 
@@ -417,17 +448,18 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
     PlanOptions po;
     po.chunk_log2 = o.chunk_log2 > 0 ? o.chunk_log2 : 20;
     po.filter = o.filter;
-    std::vector<PreparedCode> prep(count);
+    std::vector<PreparedCode> prep;
     std::vector<size_t> woffs(count);
     std::vector<PreparedCode *> ok_codes;
     std::vector<int> ok_index;
     size_t wtot = 0;
     int rounds = 0;
+    prepare_codes(codes, count, po, o.max_stage, o.work_budget, prep, status,
+                  o.plan_horizon > 0 ? o.plan_horizon : 3);
     for (int i = 0; i < count; i++) {
         woffs[i] = wtot;
         wtot += codes[i].n > 0 ? (size_t)(codes[i].n + 63) / 64 : 0;
         d[i] = -1;
-        status[i] = prepare_code(codes[i].G, codes[i].n, codes[i].k, po, o.max_stage, o.work_budget, &prep[i]);
         if (status[i] == MD_OK) {
             ok_codes.push_back(&prep[i]);
             ok_index.push_back(i);
@@ -472,6 +504,24 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
             CodeResult res;
             rc = eng.collect(c, *ok_codes[c], st[c], &res);
             const int i = ok_index[c];
+            if (res.status == MD_EAGAIN_INTERNAL) {
+                // rare: the run went past the planned stages; finish it as a single code
+                md_options oi = o;
+                oi.stream = s;
+                md_handle h = nullptr;
+                int di = -1;
+                int r2 = md_create_ex(codes[i].G, codes[i].n, codes[i].k, &oi, &h);
+                if (r2 == MD_OK) r2 = md_compute(h, &di, witness ? witness + woffs[i] : nullptr);
+                if (r2 == MD_OK) {
+                    md_info inf;
+                    md_info_get(h, &inf);
+                    if (!inf.complete) r2 = MD_EBUDGET;
+                }
+                if (h) md_destroy(h);
+                status[i] = r2;
+                d[i] = r2 == MD_OK || r2 == MD_EBUDGET ? di : -1;
+                continue;
+            }
             status[i] = res.status;
             if (res.status == MD_OK || res.status == MD_EBUDGET || res.status == MD_EUNSUPPORTED) {
                 d[i] = res.d;

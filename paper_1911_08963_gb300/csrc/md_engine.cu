@@ -4,8 +4,9 @@
 // lower bound L, the stop flag and a level cursor.  The schedule advances in ticks.  A tick
 // is three launches on one stream:
 //   prepare  -- one block: every live code that has not stopped offers the next work
-//               items of its current level (all of them, or up to a quota for time
-//               slicing); the offers are compacted per row width W with prefix sums;
+//               items of its current level (all of them, or a quota of about a fixed
+//               number of combinations, for time slicing); the offers are compacted per row
+//               width W with prefix sums;
 //   round(W) -- persistent grid per row width present: warps take tickets from one
 //               shared counter, so idle warps pick up items of any code (work stealing);
 //   post     -- one block: codes whose level is now complete apply the bound check of
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(1024) engine_prepare_kernel(const EngineArgs a
             if (cd.live && !st.stop && st.cur < cd.nlev) {
                 const BLevel &L = cd.levels[st.cur];
                 items = L.nchunks - st.next_item;
-                if (a.quota && items > a.quota) items = a.quota;
+                if (L.quota && items > L.quota) items = L.quota;
                 wc = L.W;
             }
             st.tick_items = items;

@@ -13,16 +13,22 @@ namespace mdl {
 struct PreparedCode {
     Code code;
     std::vector<LevelPlan> plans;   // level l = (g - 1) * m + j
-    int g_limit = 0;
+    int g_limit = 0;                // stages planned
+    int g_max = 0;                  // deepest stage that could be planned (C(k, g) < 2^55)
     int max_stage = 0;
     size_t header_bytes = 0;        // rows, level table, work tables, keys
     size_t h2_bytes = 0;            // pair tables
 };
 
 // Validate G, build the Gamma_j, check the work budget (estimated combinations) and plan
-// the levels.  Returns an MD_* status for this code.
+// the levels up to `horizon` stages past the estimated stopping stage (0 = every stage that
+// can be planned).  Returns an MD_* status for this code.
 int prepare_code(const uint64_t *G, int n, int k, const PlanOptions &po, int max_stage, uint64_t budget,
-                 PreparedCode *out);
+                 PreparedCode *out, int horizon = 3);
+
+// Prepare many codes on all host cores.
+void prepare_codes(const md_code *codes, int count, const PlanOptions &po, int max_stage, uint64_t budget,
+                   std::vector<PreparedCode> &out, int *status, int horizon = 3);
 
 // Per-code outcome read back from the engine.
 struct CodeResult {
@@ -39,8 +45,8 @@ class Engine {
     Engine(const Engine &) = delete;
     Engine &operator=(const Engine &) = delete;
 
-    // Slot tables for up to nslots resident codes; quota = work items per slot per tick
-    // (0 = a whole level per tick).
+    // Slot tables for up to nslots resident codes; quota = combinations a code may enumerate
+    // per tick, rounded to whole work items (0 = a whole level per tick).
     int init(int nslots, cudaStream_t stream, unsigned long long quota, int blocks_per_sm_cap);
 
     // Place codes in slots with one device allocation for all of them (owned by the
@@ -79,6 +85,7 @@ class Engine {
     int launches_ = 0;
     int sms_ = 0;
     int cap_ = 0;
+    unsigned long long quota_cw_ = 0;
     std::vector<BCode> host_codes_;
 };
 

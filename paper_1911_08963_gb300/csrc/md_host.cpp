@@ -2,57 +2,19 @@
 // validation, rank, disjoint information sets, the systematic matrices Gamma_j, the
 // packing of each Gamma_j for the device, and the per-level work plans.
 //
-// The elimination here is written for the library alone: information sets come from an
-// XOR basis of column vectors, a full-rank Gamma_j is G[:, S_j]^-1 * G, and only the
-// rank-deficient last matrix uses a Gauss-Jordan pass.
+// Each information set comes from one Gauss-Jordan pass over the still-unused columns: the
+// pass that finds k pivots leaves Gamma_j = G[:, S_j]^-1 G in its rows, and for the leftover
+// columns the pass continues into the other columns to give the reduced form
+// [[I, A], [0, B]].
 #include <algorithm>
-#include <array>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 
 #include "md_internal.h"
 
 namespace mdl {
 
 namespace {
-
-// A vector of up to 256 bits.
-struct Bits {
-    std::array<uint64_t, 4> w{};
-    bool get(int i) const { return (w[i >> 6] >> (i & 63)) & 1u; }
-    void set(int i) { w[i >> 6] |= 1ull << (i & 63); }
-    void flip(int i) { w[i >> 6] ^= 1ull << (i & 63); }
-    void operator^=(const Bits &o) { for (int t = 0; t < 4; t++) w[t] ^= o.w[t]; }
-    bool any() const { return (w[0] | w[1] | w[2] | w[3]) != 0; }
-    int top() const {  // highest set bit or -1
-        for (int t = 3; t >= 0; t--)
-            if (w[t]) return 64 * t + 63 - __builtin_clzll(w[t]);
-        return -1;
-    }
-};
-
-// Column c of G as a k-bit vector (bit i = row i).
-Bits column_of(const std::vector<uint64_t> &G, int nw, int k, int c) {
-    Bits b;
-    for (int i = 0; i < k; i++)
-        if ((G[(size_t)i * nw + c / 64] >> (c % 64)) & 1u) b.set(i);
-    return b;
-}
-
-// XOR basis keyed by the highest set bit; insert() reports whether v was independent.
-struct XorBasis {
-    std::array<Bits, 256> by_top{};
-    std::array<bool, 256> used{};
-    bool insert(Bits v) {
-        for (;;) {
-            int t = v.top();
-            if (t < 0) return false;
-            if (!used[t]) { by_top[t] = v; used[t] = true; return true; }
-            v ^= by_top[t];
-        }
-    }
-};
 
 // Pascal's triangle with saturating addition, rows 0..256.
 struct BinomTable {
@@ -110,53 +72,6 @@ int lower_bound_after(const Code &c, int g) {
 
 namespace {
 
-// Gamma_j = B^-1 G with B = G[:, S] (k x k, invertible): row i of Gamma_j is the sum of
-// the rows t of G with (B^-1)[i][t] = 1, so Gamma_j[:, S[i]] = e_i.
-std::vector<uint64_t> gamma_full(const std::vector<uint64_t> &G, int nw, int k, const std::vector<int> &S) {
-    // rows of [B | I] as bit vectors of length 2k (k <= 128 whenever 2k <= n <= 256)
-    std::vector<Bits> Brow(k), Inv(k);
-    for (int i = 0; i < k; i++) {
-        for (int t = 0; t < k; t++)
-            if ((G[(size_t)i * nw + S[t] / 64] >> (S[t] % 64)) & 1u) Brow[i].set(t);
-        Inv[i].set(i);
-    }
-    for (int col = 0; col < k; col++) {
-        int p = col;
-        while (p < k && !Brow[p].get(col)) p++;
-        std::swap(Brow[col], Brow[p]);
-        std::swap(Inv[col], Inv[p]);
-        for (int i = 0; i < k; i++)
-            if (i != col && Brow[i].get(col)) { Brow[i] ^= Brow[col]; Inv[i] ^= Inv[col]; }
-    }
-    std::vector<uint64_t> out((size_t)k * nw, 0);
-    for (int i = 0; i < k; i++)
-        for (int t = 0; t < k; t++)
-            if (Inv[i].get(t))
-                for (int w = 0; w < nw; w++) out[(size_t)i * nw + w] ^= G[(size_t)t * nw + w];
-    return out;
-}
-
-// Reduced row echelon form with the columns taken in `order` (for the leftover,
-// rank-deficient matrix Gamma_m = [[I, A], [0, B]]).
-std::vector<uint64_t> gamma_rref(const std::vector<uint64_t> &G, int nw, int k, const std::vector<int> &order) {
-    std::vector<uint64_t> A(G);
-    int r = 0;
-    for (int col : order) {
-        if (r == k) break;
-        int p = -1;
-        for (int i = r; i < k; i++)
-            if ((A[(size_t)i * nw + col / 64] >> (col % 64)) & 1u) { p = i; break; }
-        if (p < 0) continue;
-        if (p != r)
-            for (int w = 0; w < nw; w++) std::swap(A[(size_t)p * nw + w], A[(size_t)r * nw + w]);
-        for (int i = 0; i < k; i++)
-            if (i != r && ((A[(size_t)i * nw + col / 64] >> (col % 64)) & 1u))
-                for (int w = 0; w < nw; w++) A[(size_t)i * nw + w] ^= A[(size_t)r * nw + w];
-        r++;
-    }
-    return A;
-}
-
 void pack_gamma(Gamma &gm, int n, int k, int nw) {
     std::vector<char> in_set(n, 0);
     if (gm.rank == k)
@@ -169,12 +84,56 @@ void pack_gamma(Gamma &gm, int n, int k, int nw) {
     gm.W = std::max(1, (bits + 31) / 32);
     gm.WP = gm.W == 1 ? 1 : gm.W == 2 ? 2 : gm.W <= 4 ? 4 : 8;
     gm.packed.assign((size_t)k * gm.WP, 0);
+    std::vector<int> pos(n, -1);                    // column -> packed bit
+    for (int b = 0; b < bits; b++) pos[gm.packed_cols[b]] = b;
     for (int i = 0; i < k; i++)
-        for (int b = 0; b < bits; b++) {
-            int c = gm.packed_cols[b];
-            if ((gm.rows[(size_t)i * nw + c / 64] >> (c % 64)) & 1u)
-                gm.packed[(size_t)i * gm.WP + b / 32] |= 1u << (b % 32);
+        for (int w = 0; w < nw; w++) {
+            uint64_t x = gm.rows[(size_t)i * nw + w];
+            while (x) {
+                const int b = pos[64 * w + __builtin_ctzll(x)];
+                x &= x - 1;
+                if (b >= 0) gm.packed[(size_t)i * gm.WP + b / 32] |= 1u << (b % 32);
+            }
         }
+}
+
+}  // namespace
+
+namespace {
+
+// Gauss-Jordan over the columns in `order`, stopping once k pivots are found.  Returns
+// the pivot columns in the order they were found; `rows` receives the reduced matrix with
+// row i holding the i-th pivot (the reduced row echelon form for this column order).
+std::vector<int> reduce_in_order(const std::vector<uint64_t> &G, int nw, int k, const std::vector<int> &order,
+                                 std::vector<uint64_t> *rows) {
+    std::vector<uint64_t> A(G);
+    std::vector<int> piv_row;                       // row index of each pivot found so far
+    std::vector<char> used(k, 0);
+    std::vector<int> cols;
+    for (int col : order) {
+        if ((int)cols.size() == k) break;
+        const int w = col / 64;
+        const uint64_t bit = 1ull << (col % 64);
+        int p = -1;
+        for (int i = 0; i < k; i++)
+            if (!used[i] && (A[(size_t)i * nw + w] & bit)) { p = i; break; }
+        if (p < 0) continue;
+        used[p] = 1;
+        const uint64_t *pr = &A[(size_t)p * nw];
+        for (int i = 0; i < k; i++)
+            if (i != p && (A[(size_t)i * nw + w] & bit)) {
+                uint64_t *ri = &A[(size_t)i * nw];
+                for (int t = 0; t < nw; t++) ri[t] ^= pr[t];
+            }
+        piv_row.push_back(p);
+        cols.push_back(col);
+    }
+    if (rows) {
+        rows->assign((size_t)k * nw, 0);
+        for (size_t i = 0; i < piv_row.size(); i++)
+            std::memcpy(rows->data() + i * nw, &A[(size_t)piv_row[i] * nw], nw * 8);
+    }
+    return cols;
 }
 
 }  // namespace
@@ -191,36 +150,25 @@ int build_code(const uint64_t *G, int n, int k, Code *out) {
     c.n = n; c.k = k; c.nw64 = nw;
     c.G.assign(G, G + (size_t)k * nw);
 
-    // rank: insert every column into an XOR basis
-    {
-        XorBasis all;
-        int r = 0;
-        for (int col = 0; col < n && r < k; col++)
-            if (all.insert(column_of(c.G, nw, k, col))) r++;
-        if (r < k) return MD_ERANK;
-    }
-
-    // greedy disjoint information sets over the unused columns, ascending
+    // greedy disjoint information sets over the unused columns, ascending; the first pass
+    // over all columns also decides the rank
     std::vector<char> used(n, 0);
     for (;;) {
         std::vector<int> remaining;
         for (int col = 0; col < n; col++)
             if (!used[col]) remaining.push_back(col);
         if (remaining.empty()) break;
-        XorBasis basis;
-        std::vector<int> kept;
-        for (int col : remaining) {
-            if ((int)kept.size() == k) break;
-            if (basis.insert(column_of(c.G, nw, k, col))) kept.push_back(col);
-        }
         Gamma gm;
+        std::vector<int> kept = reduce_in_order(c.G, nw, k, remaining, &gm.rows);
+        if (c.gam.empty() && (int)kept.size() < k) return MD_ERANK;
         if ((int)kept.size() == k) {
+            // the pass stopped at k pivots, all inside S_j, each cleared from every other
+            // row: the rows are G[:, S_j]^-1 G with row i holding the i-th column of S_j
             gm.rank = k;
             std::vector<char> in(n, 0);
             for (int col : kept) { gm.order.push_back(col); in[col] = 1; used[col] = 1; }
             for (int col = 0; col < n; col++)
                 if (!in[col]) gm.order.push_back(col);
-            gm.rows = gamma_full(c.G, nw, k, kept);
             c.gam.push_back(std::move(gm));
             continue;
         }
@@ -230,13 +178,24 @@ int build_code(const uint64_t *G, int n, int k, Code *out) {
             for (int col : remaining) { gm.order.push_back(col); in[col] = 1; }
             for (int col = 0; col < n; col++)
                 if (!in[col]) gm.order.push_back(col);
-            gm.rows = gamma_rref(c.G, nw, k, gm.order);
+            reduce_in_order(c.G, nw, k, gm.order, &gm.rows);
             c.gam.push_back(std::move(gm));
         }
         break;
     }
     if ((int)c.gam.size() > MD_MAX_GAMMA) return MD_EUNSUPPORTED;
-    for (Gamma &gm : c.gam) pack_gamma(gm, n, k, nw);
+    // the default filter thresholds depend only on the number of packed columns
+    thread_local unsigned long long fmax_cache[kMaxN + 1];
+    thread_local bool fmax_known[kMaxN + 1] = {false};
+    for (Gamma &gm : c.gam) {
+        pack_gamma(gm, n, k, nw);
+        const int bits = (int)gm.packed_cols.size();
+        if (!fmax_known[bits]) {
+            fmax_cache[bits] = filter_thresholds(gm, 1);
+            fmax_known[bits] = true;
+        }
+        gm.fmax8 = fmax_cache[bits];
+    }
     *out = std::move(c);
     return MD_OK;
 }
@@ -306,7 +265,7 @@ LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o) {
     p.count = binom(k, g);
     p.base = gm.weight_base_is_g ? g : 0;
     p.L_after = lower_bound_after(c, g);
-    p.fmax8 = filter_thresholds(gm, o.filter);
+    p.fmax8 = o.filter == 1 ? gm.fmax8 : filter_thresholds(gm, o.filter);
     const uint64_t target_full = 1ull << std::max(8, std::min(30, o.chunk_log2));
     // keep at least ~64 work items per SM-sized slice of the level
     const uint64_t target = std::max<uint64_t>(1ull << 10, std::min<uint64_t>(target_full, p.count / (152ull * 64)));

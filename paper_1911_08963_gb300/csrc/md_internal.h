@@ -20,6 +20,7 @@ constexpr int kMaxLevels = MD_MAX_LEVELS;
 constexpr int kRankBits = 55;                 // level key = weight << 55 | colex rank
 constexpr uint64_t kRankLimit = 1ull << kRankBits;
 constexpr uint64_t kNoKey = ~0ull;
+constexpr int MD_EAGAIN_INTERNAL = 100;       // engine: the run needs stages past its plan
 
 // -------------------------------------------------------------------- host side ---
 
@@ -37,6 +38,7 @@ struct Gamma {
     int WP = 0;                     // row stride in words on the device (1, 2, 4 or 8)
     int weight_base_is_g = 0;       // 1 for full rank: weight = g + popcount(packed)
     std::vector<uint32_t> packed;   // k x WP words
+    unsigned long long fmax8 = 0;   // filter thresholds for the default mode (see plan_level)
 };
 
 struct Code {
@@ -142,6 +144,7 @@ struct BLevel {
     const MEntry *mtab;
     unsigned long long nchunks, count, per_chunk;
     unsigned long long fmax8;
+    unsigned long long quota;       // work items per tick (0 = the whole level)
     int n_m, g, v, base, kind, L_after, j, W, WP, pad0;
 };
 
@@ -172,7 +175,6 @@ struct EngineArgs {
     unsigned long long *act_total;  // [kWClasses]
     unsigned long long *tick_ctr;   // [kWClasses] work-item tickets of the current tick
     const unsigned long long *binom;// 257 x 257
-    unsigned long long quota;       // max items per slot per tick (0 = the whole level)
 };
 
 int launch_engine_prepare(const EngineArgs &a, void *stream);

@@ -3,7 +3,7 @@
 // Submissions are validated and planned on the caller's thread (so errors come back at
 // once), then queued.  One worker thread owns the GPU stream: between ticks it admits
 // queued codes into free slots while their estimated device memory fits the budget, runs
-// one tick (every resident code advances by up to `quota` work items of its current level),
+// one tick (every resident code advances by up to ~2^31 combinations of its current level),
 // reads the slot states back, and retires codes whose run has finished.  Codes admitted in
 // the middle of another code's run share every following tick with it, so their work
 // overlaps on the device; results are identical to md_compute because every code's bounds,
@@ -118,6 +118,21 @@ void md_server::run() {
             CodeResult res;
             int rc = eng.collect(s, *r.code, st[s], &res);
             eng.release(s);
+            if (rc == MD_OK && res.status == MD_EAGAIN_INTERNAL) {
+                // rare: the run went past the planned stages; finish it as a single code
+                const Code &cd = r.code->code;
+                md_options oi;
+                md_options_init(&oi);
+                oi.stream = eng.stream();
+                md_handle h = nullptr;
+                int di = -1;
+                res.witness.assign(cd.nw64, 0);
+                int r2 = md_create_ex(cd.G.data(), cd.n, cd.k, &oi, &h);
+                if (r2 == MD_OK) r2 = md_compute(h, &di, res.witness.data());
+                if (h) md_destroy(h);
+                res.status = r2;
+                res.d = r2 == MD_OK ? di : -1;
+            }
             free_slots.push_back(s);
             Done d;
             d.status = rc != MD_OK ? rc : res.status;
@@ -147,9 +162,10 @@ int md_server_create(const md_server_opts *opts, md_server **out) {
         if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess) { delete s; return MD_ECUDA; }
         stream = s->own;
     }
-    s->po.chunk_log2 = 18;                   // smaller items: finer time slices between codes
-    // time slice: at most 64 work items of each resident code per tick
-    int rc = s->eng.init(s->opts.slots, stream, 64, 0);
+    s->po.chunk_log2 = 20;
+    // time slice: about 2^31 combinations of each resident code per tick (well under a
+    // millisecond of the whole GPU), so codes that arrive wait at most a few ticks
+    int rc = s->eng.init(s->opts.slots, stream, 1ull << 31, 0);
     if (rc != MD_OK) {
         if (s->own) cudaStreamDestroy(s->own);
         delete s;

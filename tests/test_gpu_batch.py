@@ -49,6 +49,17 @@ def test_batch_matches_single_and_oracle(B, graph):
         assert di == res.d and np.array_equal(wi, res.witness), (n, k)
 
 
+def test_batch_short_plan_horizon_falls_back(B):
+    """With plans one stage past the estimate, codes that run longer are finished by
+    single-code runs; every result is still md_compute's."""
+    codes = mixed_codes()
+    d, wits, st = B.md_batch(codes, B.md_options_init(plan_horizon=1))
+    assert st == [B.MD_OK] * len(codes)
+    for (G, n, k), di, wi in zip(codes, d, wits):
+        ds, ws = single(B, G, n, k)
+        assert di == ds and np.array_equal(wi, ws), (n, k)
+
+
 def test_batch_per_code_loop_mode(B):
     codes = mixed_codes()[:8]
     a = B.md_batch(codes)

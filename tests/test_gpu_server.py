@@ -58,9 +58,12 @@ def test_server_results_equal_alone(B):
 
 
 def test_server_overlap_small_finishes_before_large(B):
+    """A small code submitted while a large one (~2e12 combinations) runs is admitted into the
+    running mix and finishes first; both results equal md_compute's."""
     s = B.md_server_create(slots=4)
     try:
-        G, n, k = I.single_code("rand128x64")
+        n, k = 176, 88
+        G = T.pack(T.random_rows(n, k, 5), n)
         tl = B.md_server_submit(s, G, n, k)
         time.sleep(0.01)
         small = (T.pack(T.random_rows(40, 12, 9), 40), 40, 12)
