@@ -129,6 +129,14 @@ def dist_env():
     return ws, rank, local
 
 
+def workload_config(args, n, k):
+    """The `config` object shared by both arms."""
+    return {"workload": "random [%d,%d] seed 3, Brouwer-Zimmermann stages g=1..%d, every level complete"
+                        % (n, k, args.max_stage),
+            "n": n, "k": k, "max_stage": args.max_stage, "filter": args.filter,
+            "l2": "flushed between steps (512 MiB write); inputs are ~100 KB"}
+
+
 def reduce_over_ranks(seconds: float, codewords: int, device: str):
     """Replicas: the slowest rank's time and all ranks' codewords (torch.distributed, any
     backend; a no-op without an initialised process group)."""
@@ -194,9 +202,7 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / len(rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
         "data": "synthetic: random code G=[I_k|R], R from SplitMix64 seed (first invertible draw)",
-        "config": {"workload": "%s: level g=%d of Gamma_1, colex prefix of %d combinations per step "
-                               "(CPU oracle, bounded sample)" % (args.workload, g, rates[0][0]),
-                   "n": n, "k": k},
+        "config": workload_config(args, n, k),
         "cpu_baseline": {"value": value, "unit": "codewords/s", "cores": threads, "kind": "oracle",
                          "sample": "colex-rank prefix of level (g=%d, Gamma_1), %d combinations per step"
                                    % (g, rates[0][0])},
@@ -290,11 +296,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic: random code G=[I_100|R], R i.i.d. Bernoulli(1/2) from SplitMix64 seed 3",
-        "config": {"workload": "random [200,100] seed 3, Brouwer-Zimmermann stages g=1..%d, every level "
-                               "complete (%d codewords per step)" % (args.max_stage, infos[0]["codewords"]),
-                   "n": n, "k": k, "max_stage": args.max_stage, "filter": args.filter,
-                   "l2": "flushed between steps (512 MiB write); inputs are ~100 KB",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": dict(workload_config(args, n, k), codewords_per_step=infos[0]["codewords"],
+                       parallelism="replicas" if ws > 1 else "single GPU"),
         "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
         "d_after_stages": infos[0]["d"],
     }

@@ -86,6 +86,18 @@ typedef struct md_options {
     int plan_horizon;         /* md_batch only: stages planned past each code's estimated
                                  stopping stage (0 = default 3); a code that needs more is
                                  finished by a single-code run, with the same result */
+    int stop_rule;            /* 0 (default) = Alg. 1: after each Gamma matrix compare U with
+                                 the L of the last complete stage; 1 = per-matrix bound: after
+                                 matrix j of stage g, L = sum_{i<=j} b_i(g) + sum_{i>j} b_i(g-1)
+                                 with b_i(g) = max(0, g+1-(k-k_i)).  Both give the same d and
+                                 witness; rule 1 can stop inside the last stage */
+    int perm_trials;          /* column orders tried before the information sets are chosen
+                                 (Section 2.2): trial 0 is the given order, trials 1.. are
+                                 Fisher-Yates shuffles driven by SplitMix64(perm_seed); the
+                                 order with the most full-rank sets, then the largest rank of
+                                 the last set, wins (earlier trial on ties).  0 or 1 = the given
+                                 order.  Outputs stay in the caller's column order. */
+    uint64_t perm_seed;
 } md_options;
 
 /* Result details of the last md_compute on a handle. */
@@ -106,6 +118,10 @@ typedef struct md_info {
     int gpu_launches;              /* kernels launched by the last md_compute */
     uint64_t h2d_bytes;            /* host-to-device bytes copied by the last md_compute */
     uint64_t d2h_bytes;            /* device-to-host bytes copied by the last md_compute */
+    uint64_t skipped_work;         /* work units left out by the mid-level stop: once U <= L
+                                      during a level, work ranked after the level's best
+                                      codeword is skipped (it cannot change d or the witness);
+                                      codewords above still counts those levels in full */
 } md_info;
 
 /* One processed level: stage g, matrix j, and the least weight of that level with its
@@ -247,6 +263,7 @@ typedef struct md_server_opts {
                                    rejected with MD_EBUDGET (0 = unlimited) */
     size_t device_bytes;        /* device memory for resident codes (0 = default 256 MiB) */
     void *stream;               /* cudaStream_t or NULL */
+    int stop_rule;              /* as md_options.stop_rule */
 } md_server_opts;
 
 int md_server_create(const md_server_opts *opts, md_server **out);

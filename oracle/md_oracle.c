@@ -348,13 +348,24 @@ enum {
     MDO_OUT_COUNT
 };
 
+/* Bound from information set j after its combinations of weight <= g are all seen:
+   every codeword not seen has at least max(0, g + 1 - (k - k_j)) nonzeros on S_j. */
+static int64_t set_bound(int g, int k, int kj) {
+    int64_t t = (int64_t)g + 1 - (k - kj);
+    return t > 0 ? t : 0;
+}
+
 /* Plain Brouwer-Zimmermann (Alg. 1 with the per-matrix check of Section 2.2).
    out: MDO_OUT_COUNT int64 values (see the enum).  witness: nw words.
    levels: per processed level (g, j, min weight, first rank of that weight, count),
    5 int64 each, at most maxlev levels.  stop_after_g > 0 truncates the run after that
    stage (used for bounded samples); 0 runs to the end.
+   stop_rule 0: Alg. 1 -- after each Gamma matrix compare with the L of the last complete
+   stage, after each stage L := sum_j max(0, g+1-(k-k_j)).  stop_rule 1: the sharper bound
+   after matrix j of stage g, sum_{i<=j} bound_i(g) + sum_{i>j} bound_i(g-1) (the matrices
+   after j have only completed stage g-1); d and the witness are the same, fewer levels run.
    Returns MDO_OK, or an error if G is invalid or a level exceeds 2^63 combinations. */
-int mdo_bz(const uint64_t *G, int n, int k, int nthreads, int stop_after_g,
+int mdo_bz(const uint64_t *G, int n, int k, int nthreads, int stop_after_g, int stop_rule,
            int64_t *out, uint64_t *witness, int64_t *levels, int maxlev) {
     if (!G || !out || !witness || n < 1 || k < 1 || k > n || n > MDO_MAXN) return MDO_EINVAL;
     int nw = words_for(n);
@@ -386,14 +397,15 @@ int mdo_bz(const uint64_t *G, int n, int k, int nthreads, int stop_after_g,
             nlev++;
             last_g = g; last_j = j;
             if (w < U) { U = w; key_g = g; key_j = j; key_rank = first; }
+            if (stop_rule == 1) {                       /* bound after matrix j of stage g */
+                L = 0;
+                for (int i = 0; i < m; i++) L += set_bound(i <= j ? g : g - 1, k, ranks[i]);
+            }
             if (L >= U) { stop = 1; break; }          /* checked after each Gamma matrix */
         }
         if (stop) break;
         L = 0;                                          /* L := sum_j max(0, g+1-(k-k_j)) */
-        for (int j = 0; j < m; j++) {
-            int64_t t = (int64_t)g + 1 - (k - ranks[j]);
-            if (t > 0) L += t;
-        }
+        for (int j = 0; j < m; j++) L += set_bound(g, k, ranks[j]);
         if (L >= U) stop = 1;
         if (stop_after_g > 0 && g >= stop_after_g) break;
     }

@@ -35,16 +35,23 @@ class OracleError(RuntimeError):
 
 
 def build(force: bool = False) -> str:
-    """Compile md_oracle.c into a shared library beside it (plain gcc, -O2)."""
+    """Compile md_oracle.c into a shared library beside it (plain gcc, -O2), under a file
+    lock so that concurrent processes build it once."""
+    import fcntl
     os.makedirs(_BUILD, exist_ok=True)
-    if (not force and os.path.exists(_LIB)
-            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
-        return _LIB
-    tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", _SRC, "-o", tmp]
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    with open(os.path.join(_BUILD, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            if (not force and os.path.exists(_LIB)
+                    and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+                return _LIB
+            tmp = _LIB + ".tmp%d" % os.getpid()
+            cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread", _SRC, "-o", tmp]
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, _LIB)
+            return _LIB
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
 
 
 def _bind(path: str):
@@ -73,7 +80,7 @@ def _bind(path: str):
     lib.mdo_scan.argtypes = [u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
                              ctypes.c_uint64, ctypes.c_int, ip, u64p]
     lib.mdo_bz.restype = ctypes.c_int
-    lib.mdo_bz.argtypes = [u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+    lib.mdo_bz.argtypes = [u64p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                            i64p, u64p, i64p, ctypes.c_int]
     return lib
 
@@ -206,14 +213,16 @@ class BZResult:
             self.d, self.key, self.L, self.m, self.stop, self.codewords)
 
 
-def bz(G, n: int, k: int, threads: int = 1, stop_after_g: int = 0, maxlev: int = 4096) -> BZResult:
-    """Plain Brouwer-Zimmermann (Alg. 1, bounds checked after each Gamma matrix)."""
+def bz(G, n: int, k: int, threads: int = 1, stop_after_g: int = 0, maxlev: int = 4096,
+       stop_rule: int = 0) -> BZResult:
+    """Plain Brouwer-Zimmermann (Alg. 1, bounds checked after each Gamma matrix);
+    stop_rule 1 uses the per-matrix bound."""
     G, p = _u64(G)
     out = np.zeros(OUT_COUNT, dtype=np.int64)
     wit = np.zeros(words(n), dtype=np.uint64)
     lev = np.zeros((maxlev, 5), dtype=np.int64)
     i64 = ctypes.POINTER(ctypes.c_int64)
-    _check(_load().mdo_bz(p, n, k, threads, stop_after_g, out.ctypes.data_as(i64),
+    _check(_load().mdo_bz(p, n, k, threads, stop_after_g, stop_rule, out.ctypes.data_as(i64),
                           wit.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
                           lev.ctypes.data_as(i64), maxlev))
     nl = min(int(out[OUT_NLEVELS]), maxlev)

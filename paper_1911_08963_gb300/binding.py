@@ -29,7 +29,8 @@ class md_options(ctypes.Structure):
     _fields_ = [("work_budget", ctypes.c_uint64), ("max_stage", ctypes.c_int), ("chunk_log2", ctypes.c_int),
                 ("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("filter", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("cancel_flag", ctypes.POINTER(ctypes.c_int)),
-                ("batch_mode", ctypes.c_int), ("use_graph", ctypes.c_int), ("plan_horizon", ctypes.c_int)]
+                ("batch_mode", ctypes.c_int), ("use_graph", ctypes.c_int), ("plan_horizon", ctypes.c_int),
+                ("stop_rule", ctypes.c_int), ("perm_trials", ctypes.c_int), ("perm_seed", ctypes.c_uint64)]
 
 
 class md_info(ctypes.Structure):
@@ -39,7 +40,7 @@ class md_info(ctypes.Structure):
                 ("key_rank", ctypes.c_uint64), ("stop_g", ctypes.c_int), ("stop_j", ctypes.c_int),
                 ("nlevels", ctypes.c_int), ("codewords", ctypes.c_uint64), ("seconds_total", ctypes.c_double),
                 ("seconds_device", ctypes.c_double), ("gpu_launches", ctypes.c_int),
-                ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64)]
+                ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64), ("skipped_work", ctypes.c_uint64)]
 
 
 class md_level(ctypes.Structure):
@@ -58,7 +59,7 @@ class md_code(ctypes.Structure):
 
 class md_server_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("work_budget", ctypes.c_uint64), ("device_bytes", ctypes.c_size_t),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("stop_rule", ctypes.c_int)]
 
 
 PROTOTYPES = {
@@ -233,8 +234,9 @@ def md_batch(codes, options: md_options | None = None):
     return list(d), wits, list(st)
 
 
-def md_server_create(slots: int = 0, work_budget: int = 0, device_bytes: int = 0, stream=None) -> int:
-    o = md_server_opts(slots, work_budget, device_bytes, stream)
+def md_server_create(slots: int = 0, work_budget: int = 0, device_bytes: int = 0, stream=None,
+                     stop_rule: int = 0) -> int:
+    o = md_server_opts(slots, work_budget, device_bytes, stream, stop_rule)
     s = ctypes.c_void_p()
     _check(lib.md_server_create(ctypes.byref(o), ctypes.byref(s)), "md_server_create")
     return s.value

@@ -44,8 +44,19 @@ def _stale(target, deps):
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile what is stale, under a file lock (several ranks may call this at once)."""
+    import fcntl
     os.makedirs(OBJDIR, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
+    with open(os.path.join(LIBDIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     cc = nvcc()
     headers = _deps()
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]

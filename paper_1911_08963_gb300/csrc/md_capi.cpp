@@ -111,6 +111,7 @@ int setup_device(md_ctx *h) {
     PlanOptions po;
     po.chunk_log2 = h->opt.chunk_log2 > 0 ? h->opt.chunk_log2 : 20;
     po.filter = h->opt.filter;
+    po.stop_rule = h->opt.stop_rule;
     h->g_limit = 0;
     for (int g = 1; g <= std::min(k, kMaxG); g++) {
         if (binom(k, g) >= kRankLimit) break;
@@ -239,6 +240,7 @@ LevelArgs level_args(md_ctx *h, const LevelPlan &p, int level, bool h2s) {
     a.m_total = (int)h->code.gam.size();
     a.j = p.j;
     a.L_after = p.L_after;
+    a.L_first = p.L_first;
     a.check_stop = 1;
     (void)gm;
     return a;
@@ -282,9 +284,9 @@ int md_create_ex(const uint64_t *G, int n, int k, const md_options *opt, md_hand
     if (!G || !out) return MD_EINVAL;
     md_ctx *h = new (std::nothrow) md_ctx();
     if (!h) return MD_ENOMEM;
-    int rc = build_code(G, n, k, &h->code);
-    if (rc != MD_OK) { delete h; return rc; }
     if (opt) h->opt = *opt; else md_options_init(&h->opt);
+    int rc = build_code_permuted(G, n, k, h->opt.perm_trials, h->opt.perm_seed, &h->code);
+    if (rc != MD_OK) { delete h; return rc; }
     fill_static_info(h);
     *out = h;
     return MD_OK;
@@ -314,9 +316,12 @@ int md_levels(md_handle h, md_level *levels, int max, int *count) {
 
 int md_gamma(md_handle h, int j, uint64_t *gamma, int *order) {
     if (!h || j < 0 || j >= (int)h->code.gam.size()) return MD_EINVAL;
-    const Gamma &gm = h->code.gam[j];
-    if (gamma) std::memcpy(gamma, gm.rows.data(), gm.rows.size() * 8);
-    if (order) std::memcpy(order, gm.order.data(), gm.order.size() * sizeof(int));
+    const Code &c = h->code;
+    const Gamma &gm = c.gam[j];
+    if (gamma)
+        for (int i = 0; i < c.k; i++) to_caller_order(c, &gm.rows[(size_t)i * c.nw64], gamma + (size_t)i * c.nw64);
+    if (order)
+        for (int p = 0; p < c.n; p++) order[p] = c.perm.empty() ? gm.order[p] : c.perm[gm.order[p]];
     return MD_OK;
 }
 
@@ -433,6 +438,7 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
     h->info.seconds_device = ms * 1e-3;
     h->info.gpu_launches = launches + h->setup_launches;
     h->info.h2d_bytes = h2d + h->setup_h2d;
+    h->info.skipped_work = st.skipped;
     h->info.d2h_bytes = d2h;
     h->setup_launches = 0;
     h->setup_h2d = 0;
@@ -455,7 +461,7 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
     h->info.seconds_total = seconds_since(t0);
     if (status != MD_OK) return status;
     *d = U;
-    if (witness) std::memcpy(witness, wv.data(), wv.size() * 8);
+    if (witness) to_caller_order(c, wv.data(), witness);
     return MD_OK;
 }
 
@@ -468,6 +474,7 @@ int md_level_plan(md_handle h, int g, int j, int *kind, md_task_info *tasks, int
     PlanOptions po;
     po.chunk_log2 = h->opt.chunk_log2 > 0 ? h->opt.chunk_log2 : 20;
     po.filter = h->opt.filter;
+    po.stop_rule = h->opt.stop_rule;
     LevelPlan p = plan_level(c, g, j, po);
     *kind = p.kind;
     *work_items = p.nchunks;
@@ -538,6 +545,7 @@ int md_scan_task(md_handle h, int g, int j, int M, uint64_t u0, uint64_t u1, int
     PlanOptions po;
     po.chunk_log2 = h->opt.chunk_log2 > 0 ? h->opt.chunk_log2 : 20;
     po.filter = h->opt.filter;
+    po.stop_rule = h->opt.stop_rule;
     LevelPlan p = plan_level(c, g, j, po);
     if (p.kind == KIND_SIMPLE) p.kind = (g == 5) ? KIND_SPLIT2 : KIND_SPLIT3, p.v = g - p.kind - 1;
     const int P = p.kind;

@@ -213,7 +213,24 @@ struct ChunkCtx {
     unsigned long long fmax8;      // byte f-1: 1 + largest threshold for an f-word filter
     const unsigned long long *tb;
     int stride;
+    // mid-level stop (may be null): the code's lower bound of completed stages and this
+    // level's key; `skipped` counts upper parts (or rank runs) left out
+    const int *L;
+    const unsigned long long *key;
+    unsigned long long *skipped;
 };
+
+// Once U <= L the minimum distance is U: no codeword lighter than U exists.  This level then
+// holds the first codeword of weight U (it lowered U to L or below), and work whose ranks all
+// exceed the level's best rank cannot change the result.  Returns that rank, or ~0.
+__device__ __forceinline__ unsigned long long skip_above(const ChunkCtx &c, const unsigned int *U) {
+    if (!c.L) return ~0ull;
+    const int u = (int)*(volatile const unsigned int *)U;
+    if (u > *(volatile const int *)c.L) return ~0ull;
+    const unsigned long long key = *(volatile const unsigned long long *)c.key;
+    if (key == kNoKey || (int)(key >> kRankBits) != u) return ~0ull;
+    return key & (kRankLimit - 1);
+}
 
 // Colex state of a lane's next upper part (v elements of [0, K'), column M + 1 + element),
 // its row sum and the rank of its first head.
@@ -296,8 +313,16 @@ __device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, 
     for (int w = 0; w < W; w++) up.S[w] = 0;
     up.R = 0;
     if (remaining > 0) up.start(c, rows, M, e.upper_base + my_lo);
+    // the completed stages' bound does not change during a level: the mid-level stop can only
+    // apply once U has come down to it
+    const int Lfix = c.L ? *(volatile const int *)c.L : -1;
 
     for (long long it = 0; it < (long long)per_lane; it += NU) {
+        // a lane whose next upper part starts above the rank that settles the run stops
+        if (remaining > 0 && Usnap <= Lfix && up.R > skip_above(c, U)) {
+            if (c.skipped) atomicAdd(c.skipped, (unsigned long long)remaining);
+            remaining = 0;
+        }
         const bool on = remaining > 0;
         if (!__any_sync(kFull, on)) break;
         // NU upper parts of this lane; past the lane's end the last one is repeated (a repeat
@@ -331,11 +356,19 @@ __device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, 
                 unsigned long long rb[NU];
                 rows.load(c3, rw);
                 const unsigned long long h3 = (unsigned long long)c3 * (c3 - 1) * (c3 - 2) / 6;
+                unsigned long long rmin = ~0ull;
 #pragma unroll
                 for (int q = 0; q < NU; q++) {
 #pragma unroll
                     for (int w = 0; w < W; w++) T[q][w] = S[q][w] ^ rw[w];
                     rb[q] = R[q] + h3;
+                    rmin = min(rmin, rb[q]);
+                }
+                // heads are walked in rank order: once every lane's next rank lies above the
+                // rank that settles the run, the rest of this upper part's heads can go
+                if (__any_sync(kFull, Usnap <= Lfix) && __all_sync(kFull, !on || rmin > skip_above(c, U))) {
+                    if (c.skipped && (threadIdx.x & 31) == 0) atomicAdd(c.skipped, 1ull);
+                    break;
                 }
                 const int n2 = c3 * (c3 - 1) / 2;
                 walk_dispatch<W, WP, NU>(F, h2, T, n2, thr, c.base, best, rb);
@@ -353,9 +386,13 @@ __device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, 
 // One work item of a small level: each lane walks its own run of colex ranks [lo, hi)
 // with the colex successor, updating the row sum by the rows that leave and enter.
 template <int W, int WP, class RowSrc>
-__device__ __forceinline__ void simple_chunk(const ChunkCtx &c, unsigned long long lo, unsigned long long hi,
+__device__ __forceinline__ void simple_chunk(const ChunkCtx &c, unsigned long long lo, const unsigned long long hi,
                                              const RowSrc &rows, unsigned int *U, int &Usnap, LaneBest &best) {
     const int g = c.g;
+    if (lo < hi && lo > skip_above(c, U)) {
+        if (c.skipped) atomicAdd(c.skipped, 1ull);
+        lo = hi;
+    }
     if (lo < hi) {
         int cc[kMaxG];
         unsigned long long r = lo;

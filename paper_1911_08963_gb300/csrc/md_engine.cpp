@@ -18,7 +18,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 int prepare_code(const uint64_t *G, int n, int k, const PlanOptions &po, int max_stage, uint64_t budget,
                  PreparedCode *out, int horizon) {
     PreparedCode p;
-    int rc = build_code(G, n, k, &p.code);
+    int rc = build_code_permuted(G, n, k, po.perm_trials, po.perm_seed, &p.code);
     if (rc != MD_OK) return rc;
     int g_est = 0;
     const double work = estimate_work(p.code, nullptr, &g_est);
@@ -164,6 +164,7 @@ int Engine::fill_code(PreparedCode &pc, char *header, char *h2, std::vector<char
             L.quota = std::max<unsigned long long>(1, quota_cw_ / per_item);
         }
         L.L_after = p.L_after;
+        L.L_first = p.L_first;
         L.j = p.j;
         L.W = cd.gam[p.j].W;
         L.WP = cd.gam[p.j].WP;
@@ -183,6 +184,8 @@ int Engine::fill_code(PreparedCode &pc, char *header, char *h2, std::vector<char
     return MD_OK;
 }
 
+// Stream-ordered: the copies from pageable host memory are staged before the calls return,
+// and the next tick on the same stream sees them.
 int Engine::write_slot(int slot, const BCode &bc, const BState &bs) {
     host_codes_[slot] = bc;
     if (cudaMemcpyAsync((void *)(args_.codes + slot), &host_codes_[slot], sizeof(BCode), cudaMemcpyHostToDevice,
@@ -190,7 +193,7 @@ int Engine::write_slot(int slot, const BCode &bc, const BState &bs) {
         return MD_ECUDA;
     if (cudaMemcpyAsync(args_.states + slot, &bs, sizeof(BState), cudaMemcpyHostToDevice, stream_) != cudaSuccess)
         return MD_ECUDA;
-    return cudaStreamSynchronize(stream_) == cudaSuccess ? MD_OK : MD_ECUDA;
+    return MD_OK;
 }
 
 // Build the pair tables of the given matrices (groups of up to 256 per launch).
@@ -288,23 +291,24 @@ int Engine::load_many(const std::vector<PreparedCode *> &codes, const std::vecto
 int Engine::load_one(PreparedCode &pc, int slot) {
     if (slot < 0 || slot >= nslots_) return MD_EINVAL;
     char *mem = nullptr;
-    if (cudaMalloc(&mem, std::max<size_t>(256, pc.header_bytes + pc.h2_bytes)) != cudaSuccess) {
+    // stream-ordered allocation from the device's memory pool: no device-wide synchronisation
+    if (cudaMallocAsync((void **)&mem, std::max<size_t>(256, pc.header_bytes + pc.h2_bytes), stream_) != cudaSuccess) {
         cudaGetLastError();
         return MD_ENOMEM;
     }
     std::vector<char> img(pc.header_bytes, 0);
     BCode bc{};
     int rc = fill_code(pc, mem, mem + pc.header_bytes, img, 0, &bc);
-    if (rc != MD_OK) { cudaFree(mem); return rc; }
+    if (rc != MD_OK) { cudaFreeAsync(mem, stream_); return rc; }
     if (cudaMemcpyAsync(mem, img.data(), img.size(), cudaMemcpyHostToDevice, stream_) != cudaSuccess) {
-        cudaFree(mem);
+        cudaFreeAsync(mem, stream_);
         return MD_ECUDA;
     }
     size_t roff = 0, hoff = 0;
     for (const Gamma &gm : pc.code.gam) {
         if (launch_h2_build((const uint32_t *)(mem + roff), (uint32_t *)(mem + pc.header_bytes + hoff), pc.code.k,
                             gm.WP, stream_) != 0) {
-            cudaFree(mem);
+            cudaFreeAsync(mem, stream_);
             return MD_ECUDA;
         }
         roff = align256(roff + (size_t)pc.code.k * gm.WP * 4);
@@ -315,17 +319,44 @@ int Engine::load_one(PreparedCode &pc, int slot) {
     return write_slot(slot, bc, bs);
 }
 
-int Engine::tick() {
-    bool ok = launch_engine_prepare(args_, stream_) == 0;
-    launches_++;
-    for (int w = 1; w < kWClasses; w++)
-        if (wclass_[w]) {
-            ok &= launch_engine_round(args_, w, blocks_[w], kThreads, stream_) == 0;
-            launches_++;
-        }
-    ok &= launch_engine_post(args_, stream_) == 0;
-    launches_++;
+int Engine::enqueue_ticks(int repeats) {
+    bool ok = true;
+    for (int r = 0; r < repeats; r++) {
+        ok &= launch_engine_prepare(args_, stream_) == 0;
+        launches_++;
+        for (int w = 1; w < kWClasses; w++)
+            if (wclass_[w]) {
+                ok &= launch_engine_round(args_, w, blocks_[w], kThreads, stream_) == 0;
+                launches_++;
+            }
+        ok &= launch_engine_post(args_, stream_) == 0;
+        launches_++;
+    }
     return ok ? MD_OK : MD_ECUDA;
+}
+
+int Engine::tick(int repeats, bool use_graph) {
+    if (!use_graph) return enqueue_ticks(repeats);
+    unsigned mask = 0;
+    for (int w = 1; w < kWClasses; w++)
+        if (wclass_[w]) mask |= 1u << w;
+    if (!graph_ || mask != graph_mask_ || repeats != graph_repeats_) {
+        if (graph_) { cudaGraphExecDestroy(graph_); graph_ = nullptr; }
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MD_ECUDA;
+        int rc = enqueue_ticks(repeats);
+        if (cudaStreamEndCapture(stream_, &g) != cudaSuccess || rc != MD_OK) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return MD_ECUDA;
+        }
+        const bool ok = cudaGraphInstantiate(&graph_, g, 0) == cudaSuccess;
+        cudaGraphDestroy(g);
+        if (!ok) { cudaGetLastError(); graph_ = nullptr; return MD_ECUDA; }
+        graph_mask_ = mask;
+        graph_repeats_ = repeats;
+    }
+    return cudaGraphLaunch(graph_, stream_) == cudaSuccess ? MD_OK : MD_ECUDA;
 }
 
 int Engine::read_states(std::vector<BState> &out) {
@@ -357,6 +388,7 @@ int Engine::collect(int slot, const PreparedCode &pc, const BState &st, CodeResu
     for (int r : comb)
         for (int w = 0; w < cd.nw64; w++) res->witness[w] ^= cd.gam[kp.j].rows[(size_t)r * cd.nw64 + w];
     if (popcount_row(res->witness.data(), cd.nw64) != U) { res->status = MD_EINTERNAL; return MD_OK; }
+    to_caller_order(cd, res->witness.data(), res->witness.data());
     res->d = U;
     res->status = MD_OK;
     if (!res->complete) {
@@ -373,20 +405,20 @@ int Engine::release(int slot) {
     host_codes_[slot] = off;
     int rc = MD_OK;
     if (cudaMemcpyAsync((void *)(args_.codes + slot), &host_codes_[slot], sizeof(BCode), cudaMemcpyHostToDevice,
-                        stream_) != cudaSuccess ||
-        cudaStreamSynchronize(stream_) != cudaSuccess)
+                        stream_) != cudaSuccess)
         rc = MD_ECUDA;
     if (own_mem_[slot]) {
-        cudaFree(own_mem_[slot]);
+        cudaFreeAsync(own_mem_[slot], stream_);      // after every kernel queued so far
         own_mem_[slot] = nullptr;
     }
     return rc;
 }
 
 void Engine::release_all() {
-    if (stream_) cudaStreamSynchronize(stream_);
+    if (graph_) { cudaGraphExecDestroy(graph_); graph_ = nullptr; }
     for (char *&p : own_mem_)
-        if (p) { cudaFree(p); p = nullptr; }
+        if (p) { cudaFreeAsync(p, stream_); p = nullptr; }
+    if (stream_) cudaStreamSynchronize(stream_);
     for (char *p : shared_mem_) cudaFree(p);
     shared_mem_.clear();
     if (tables_) cudaFree(tables_);
@@ -448,6 +480,9 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
     PlanOptions po;
     po.chunk_log2 = o.chunk_log2 > 0 ? o.chunk_log2 : 20;
     po.filter = o.filter;
+    po.stop_rule = o.stop_rule;
+    po.perm_trials = o.perm_trials;
+    po.perm_seed = o.perm_seed;
     std::vector<PreparedCode> prep;
     std::vector<size_t> woffs(count);
     std::vector<PreparedCode *> ok_codes;

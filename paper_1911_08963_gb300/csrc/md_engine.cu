@@ -54,7 +54,8 @@ __global__ void __launch_bounds__(kEngineThreads) engine_round_kernel(const Engi
         const unsigned long long item = *(volatile const unsigned long long *)&stv.next_item + ticket -
                                         (lo ? __ldg(prefix + lo - 1) : 0ull);
         const BLevel L = cd.levels[cur];
-        const ChunkCtx c{cd.k, L.g, L.v, L.base, L.fmax8, a.binom, kBinomStride};
+        const ChunkCtx c{cd.k, L.g, L.v, L.base, L.fmax8, a.binom, kBinomStride, &a.states[slot].L, &cd.keys[cur],
+                         nullptr};
         unsigned int *U = &a.states[slot].U;
         int Usnap = (int)*(volatile unsigned int *)U;
         const GlobSrc<W, WP> rows{L.rows};
@@ -105,6 +106,7 @@ __global__ void __launch_bounds__(1024) engine_prepare_kernel(const EngineArgs a
     __shared__ int wt_int[32];
     __shared__ int run_count[kWClasses];
     __shared__ unsigned long long run_total[kWClasses];
+    __shared__ unsigned int present;            // row widths offered in this tile
     if (threadIdx.x < kWClasses) {
         run_count[threadIdx.x] = 0;
         run_total[threadIdx.x] = 0;
@@ -126,7 +128,13 @@ __global__ void __launch_bounds__(1024) engine_prepare_kernel(const EngineArgs a
             }
             st.tick_items = items;
         }
+        if (threadIdx.x == 0) present = 0;
+        __syncthreads();
+        if (items > 0) atomicOr(&present, 1u << wc);
+        __syncthreads();
+        const unsigned int mask = present;
         for (int w = 1; w < kWClasses; w++) {
+            if (!((mask >> w) & 1u)) continue;          // block-uniform: no slot of this width
             const int flag = (wc == w && items > 0) ? 1 : 0;
             int nflag = 0;
             unsigned long long ntot = 0;
@@ -143,6 +151,7 @@ __global__ void __launch_bounds__(1024) engine_prepare_kernel(const EngineArgs a
             }
             __syncthreads();
         }
+        __syncthreads();                            // every thread has read `present`
     }
     if (threadIdx.x < kWClasses) {
         a.act_count[threadIdx.x] = run_count[threadIdx.x];
@@ -162,10 +171,11 @@ __global__ void engine_post_kernel(const EngineArgs a) {
             // level complete: the bound check after each Gamma matrix, L(g) after a stage
             st.last_level = st.cur;
             const int U = (int)st.U;
+            if (L.L_first && L.L_after >= 0) st.L = max(st.L, L.L_after);   // per-matrix bound
             if (st.L >= U) {
                 st.stop = 1;
-            } else if (L.j == cd.m - 1) {
-                st.L = L.L_after;
+            } else if (L.L_after >= 0) {
+                st.L = max(st.L, L.L_after);
                 if (st.L >= U) st.stop = 1;
             }
             st.cur += 1;

@@ -55,8 +55,10 @@ class Engine {
     // Place one code in a slot with its own device allocation (released by release).
     int load_one(PreparedCode &code, int slot);
 
-    // Enqueue one tick (prepare, one round per row width present, post).
-    int tick();
+    // Enqueue `repeats` ticks (prepare, one round per row width present, post), as one
+    // captured CUDA graph when use_graph is set (re-captured when the set of row widths
+    // present changes).
+    int tick(int repeats = 1, bool use_graph = false);
     // Copy the slot states to the host (synchronises the stream).
     int read_states(std::vector<BState> &out);
     // Result of the code in `slot` (its keys are read back); state from read_states.
@@ -86,6 +88,10 @@ class Engine {
     int sms_ = 0;
     int cap_ = 0;
     unsigned long long quota_cw_ = 0;
+    cudaGraphExec_t graph_ = nullptr;
+    unsigned graph_mask_ = 0;
+    int graph_repeats_ = 0;
+    int enqueue_ticks(int repeats);
     std::vector<BCode> host_codes_;
 };
 

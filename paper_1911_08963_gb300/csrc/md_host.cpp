@@ -7,6 +7,7 @@
 // columns the pass continues into the other columns to give the reduced form
 // [[I, A], [0, B]].
 #include <algorithm>
+#include <utility>
 #include <cmath>
 #include <cstring>
 
@@ -200,6 +201,90 @@ int build_code(const uint64_t *G, int n, int k, Code *out) {
     return MD_OK;
 }
 
+namespace {
+
+struct SplitMix64 {
+    uint64_t state;
+    uint64_t next() {
+        state += 0x9E3779B97F4A7C15ull;
+        uint64_t z = state;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+};
+
+// The columns of G (k x n, nw words per row) taken in `order`.
+std::vector<uint64_t> permute_columns(const uint64_t *G, int n, int k, const std::vector<int> &order) {
+    const int nw = (n + 63) / 64;
+    std::vector<uint64_t> out((size_t)k * nw, 0);
+    for (int i = 0; i < k; i++)
+        for (int p = 0; p < n; p++) {
+            const int c = order[p];
+            if ((G[(size_t)i * nw + c / 64] >> (c % 64)) & 1u) out[(size_t)i * nw + p / 64] |= 1ull << (p % 64);
+        }
+    return out;
+}
+
+// (number of full-rank information sets, rank of the last set) for the greedy sets taken
+// in the given column order.
+std::pair<int, int> set_profile(const std::vector<uint64_t> &G, int n, int k) {
+    const int nw = (n + 63) / 64;
+    std::vector<char> used(n, 0);
+    int full = 0, last = 0;
+    for (;;) {
+        std::vector<int> remaining;
+        for (int col = 0; col < n; col++)
+            if (!used[col]) remaining.push_back(col);
+        if (remaining.empty()) break;
+        std::vector<int> kept = reduce_in_order(G, nw, k, remaining, nullptr);
+        if ((int)kept.size() == k) {
+            full++;
+            for (int col : kept) used[col] = 1;
+            continue;
+        }
+        last = (int)kept.size();
+        break;
+    }
+    return {full, last};
+}
+
+}  // namespace
+
+int build_code_permuted(const uint64_t *G, int n, int k, int trials, uint64_t seed, Code *out) {
+    if (trials <= 1) return build_code(G, n, k, out);
+    if (!G || !out || n < 1 || k < 1 || k > n) return MD_EINVAL;
+    if (n > kMaxN) return MD_EUNSUPPORTED;
+    std::vector<int> order(n), best;
+    for (int i = 0; i < n; i++) order[i] = i;
+    SplitMix64 rng{seed};
+    std::pair<int, int> best_score{-1, -1};
+    for (int t = 0; t < trials; t++) {
+        if (t > 0)
+            for (int i = n - 1; i >= 1; i--) std::swap(order[i], order[(int)(rng.next() % (uint64_t)(i + 1))]);
+        const std::pair<int, int> sc = set_profile(permute_columns(G, n, k, order), n, k);
+        if (sc > best_score) { best_score = sc; best = order; }
+    }
+    std::vector<uint64_t> Gp = permute_columns(G, n, k, best);
+    int rc = build_code(Gp.data(), n, k, out);
+    if (rc != MD_OK) return rc;
+    bool identity = true;
+    for (int i = 0; i < n; i++) identity &= best[i] == i;
+    if (!identity) out->perm = best;
+    return MD_OK;
+}
+
+void to_caller_order(const Code &c, const uint64_t *row, uint64_t *out) {
+    if (c.perm.empty()) {
+        std::memcpy(out, row, (size_t)c.nw64 * 8);
+        return;
+    }
+    std::vector<uint64_t> tmp((size_t)c.nw64, 0);
+    for (int p = 0; p < c.n; p++)
+        if ((row[p / 64] >> (p % 64)) & 1u) tmp[c.perm[p] / 64] |= 1ull << (c.perm[p] % 64);
+    std::memcpy(out, tmp.data(), (size_t)c.nw64 * 8);
+}
+
 double estimate_work(const Code &c, int *d_est, int *g_stop) {
     // expected number of codewords of weight <= w in a random [n, k] code
     double acc = 0.0;
@@ -264,7 +349,16 @@ LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o) {
     p.g = g; p.j = j;
     p.count = binom(k, g);
     p.base = gm.weight_base_is_g ? g : 0;
-    p.L_after = lower_bound_after(c, g);
+    if (o.stop_rule == 1) {
+        // matrices up to j have completed stage g, the later ones stage g - 1
+        int L = 0;
+        for (int i = 0; i < (int)c.gam.size(); i++)
+            L += std::max(0, (i <= j ? g : g - 1) + 1 - (k - c.gam[i].rank));
+        p.L_after = L;
+        p.L_first = 1;
+    } else {
+        p.L_after = j == (int)c.gam.size() - 1 ? lower_bound_after(c, g) : -1;
+    }
     p.fmax8 = o.filter == 1 ? gm.fmax8 : filter_thresholds(gm, o.filter);
     const uint64_t target_full = 1ull << std::max(8, std::min(30, o.chunk_log2));
     // keep at least ~64 work items per SM-sized slice of the level

@@ -43,12 +43,23 @@ struct Gamma {
 
 struct Code {
     int n = 0, k = 0, nw64 = 0;
-    std::vector<uint64_t> G;
+    std::vector<uint64_t> G;        // in the processing column order (see perm)
     std::vector<Gamma> gam;
+    std::vector<int> perm;          // processing position -> caller's column (empty: identity)
 };
 
 // Validate, check rank, find the information sets and build every Gamma_j.
 int build_code(const uint64_t *G, int n, int k, Code *out);
+
+// As build_code, after choosing a column order (Section 2.2: random column permutations, the
+// one with the most full-rank information sets and then the largest rank of the last set).
+// trials <= 1: the caller's order.  Trial 0 is the caller's order; trial t >= 1 is a
+// Fisher-Yates shuffle driven by SplitMix64(seed) (one stream for all trials: for i = n-1
+// down to 1, swap position i with position next() mod (i+1)).  Ties keep the earlier trial.
+int build_code_permuted(const uint64_t *G, int n, int k, int trials, uint64_t seed, Code *out);
+
+// A row in the processing order -> the caller's column order.
+void to_caller_order(const Code &c, const uint64_t *row, uint64_t *out);
 
 uint64_t binom(int a, int b);                   // saturating at UINT64_MAX
 void colex_unrank(uint64_t r, int g, int k, int *c);
@@ -76,7 +87,8 @@ struct LevelPlan {
     int kind = KIND_SIMPLE;         // 0 = per-lane rank ranges; 2, 3 = head size P
     int v = 0;                      // upper elements per lane (kinds 2, 3)
     int base = 0;                   // weight base (g or 0)
-    int L_after = 0;                // lower bound after this stage (used when j = m - 1)
+    int L_after = -1;               // lower bound once this level is complete (-1: unchanged)
+    int L_first = 0;                // 1: raise L before the check after this level (rule 1)
     // filter thresholds: byte f-1 holds 1 + the largest packed-weight threshold at which the
     // popcount of the OR of the first f words still rejects almost every codeword (0 = never)
     unsigned long long fmax8 = 0;
@@ -87,6 +99,9 @@ struct LevelPlan {
 };
 
 struct PlanOptions {
+    int stop_rule = 0;              // 0: Alg. 1 stage bound; 1: per-matrix bound
+    int perm_trials = 0;            // column orders tried (build_code_permuted)
+    uint64_t perm_seed = 0;
     int chunk_log2 = 20;
     int filter = 1;                 // 0 = never, 1 = when it pays, 2 = always
 };
@@ -107,7 +122,8 @@ struct DevState {
     int stop;                       // set once L >= U
     int error;                      // device-side error code (0 = none)
     int last_level;                 // last level finalised
-    int pad[3];
+    int pad;
+    unsigned long long skipped;     // work left out by the mid-level stop
     unsigned int u_in[kMaxLevels];  // U when each level started
     unsigned long long key[kMaxLevels];   // per-level least (weight << 55 | first rank)
     unsigned long long ctr[kMaxLevels];   // per-level work-item counters
@@ -131,6 +147,7 @@ struct LevelArgs {
     int m_total;                    // number of Gamma matrices
     int j;
     int L_after;
+    int L_first;
     int check_stop;                 // 0 for md_scan_range (no stop logic)
 };
 
@@ -145,7 +162,7 @@ struct BLevel {
     unsigned long long nchunks, count, per_chunk;
     unsigned long long fmax8;
     unsigned long long quota;       // work items per tick (0 = the whole level)
-    int n_m, g, v, base, kind, L_after, j, W, WP, pad0;
+    int n_m, g, v, base, kind, L_after, j, W, WP, L_first;
 };
 
 // A slot of the engine: one resident code (written by the host on admission).

@@ -53,7 +53,8 @@ __global__ void __launch_bounds__(kThreads, 1) split_kernel(const LevelArgs a) {
 
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
     const SmemSrc<W, WP> rows{sbase};
-    const ChunkCtx c{k, a.g, a.v, a.base, a.fmax8, a.binom, k + 1};
+    const ChunkCtx c{k, a.g, a.v, a.base, a.fmax8, a.binom, k + 1,
+                     a.check_stop ? &st->L : nullptr, &st->key[a.level], &st->skipped};
     const int lane = threadIdx.x & 31;
     int Usnap = (int)*(volatile unsigned int *)&st->U;
 
@@ -87,7 +88,8 @@ __global__ void __launch_bounds__(kThreads, 1) simple_kernel(const LevelArgs a) 
     stage_to_smem(smem, a.rows, k * WP);
     __syncthreads();
     const SmemSrc<W, WP> rows{(uint32_t)__cvta_generic_to_shared(smem)};
-    const ChunkCtx c{k, a.g, a.v, a.base, a.fmax8, a.binom, k + 1};
+    const ChunkCtx c{k, a.g, a.v, a.base, a.fmax8, a.binom, k + 1,
+                     a.check_stop ? &st->L : nullptr, &st->key[a.level], &st->skipped};
     const int lane = threadIdx.x & 31;
     int Usnap = (int)*(volatile unsigned int *)&st->U;
     for (;;) {
@@ -126,9 +128,10 @@ __global__ void finalize_kernel(const LevelArgs a) {
     st->last_level = a.level;
     const int U = (int)st->U;
     if (a.level + 1 < kMaxLevels) st->u_in[a.level + 1] = (unsigned int)U;
+    if (a.L_first && a.L_after >= 0) st->L = max(st->L, a.L_after);   // per-matrix bound
     if (st->L >= U) { st->stop = 1; return; }
-    if (a.j == a.m_total - 1) {
-        st->L = a.L_after;
+    if (a.L_after >= 0) {                       // the bound this level completes
+        st->L = max(st->L, a.L_after);
         if (st->L >= U) st->stop = 1;
     }
 }
@@ -146,6 +149,7 @@ __global__ void state_init_kernel(DevState *st, unsigned int u0) {
         st->stop = 0;
         st->error = 0;
         st->last_level = -1;
+        st->skipped = 0;
     }
 }
 

@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kThreads) noalloc_scan_kernel(const uint32_t *
     stage_to_smem(smem, rows_g, k * WP);
     __syncthreads();
     const SmemSrc<W, WP> rows{(uint32_t)__cvta_generic_to_shared(smem)};
-    const ChunkCtx c{k, g, 0, base, 0ull, tb, kNoAllocMaxK + 1};
+    const ChunkCtx c{k, g, 0, base, 0ull, tb, kNoAllocMaxK + 1, nullptr, nullptr, nullptr};
     const int lane = threadIdx.x & 31;
     int Usnap = (int)*(volatile unsigned int *)&st->U;
     for (;;) {

@@ -3,7 +3,8 @@
 // Submissions are validated and planned on the caller's thread (so errors come back at
 // once), then queued.  One worker thread owns the GPU stream: between ticks it admits
 // queued codes into free slots while their estimated device memory fits the budget, runs
-// one tick (every resident code advances by up to ~2^31 combinations of its current level),
+// eight ticks (in each, every resident code advances by up to ~2^28 combinations of its
+// current level, and by at most one level),
 // reads the slot states back, and retires codes whose run has finished.  Codes admitted in
 // the middle of another code's run share every following tick with it, so their work
 // overlaps on the device; results are identical to md_compute because every code's bounds,
@@ -38,6 +39,8 @@ struct Done {
 };
 
 }  // namespace
+
+constexpr int kTicksPerRound = 8;
 
 struct md_server {
     md_server_opts opts{};
@@ -99,7 +102,9 @@ void md_server::run() {
             resident[slot] = std::move(r);
         }
         if (resident.empty()) continue;
-        if (eng.tick() != MD_OK || eng.read_states(st) != MD_OK) {
+        // eight ticks per host round trip, one graph launch: a code with small levels moves
+        // through up to eight levels between two looks from the host
+        if (eng.tick(kTicksPerRound, true) != MD_OK || eng.read_states(st) != MD_OK) {
             std::lock_guard<std::mutex> lk(mu);
             fatal = MD_ECUDA;
             for (auto &kv : resident) { Done d; d.status = MD_ECUDA; done[kv.second.ticket] = std::move(d); }
@@ -162,10 +167,12 @@ int md_server_create(const md_server_opts *opts, md_server **out) {
         if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess) { delete s; return MD_ECUDA; }
         stream = s->own;
     }
-    s->po.chunk_log2 = 20;
-    // time slice: about 2^31 combinations of each resident code per tick (well under a
-    // millisecond of the whole GPU), so codes that arrive wait at most a few ticks
-    int rc = s->eng.init(s->opts.slots, stream, 1ull << 31, 0);
+    // small work items keep the idle tail at the end of every tick short
+    s->po.chunk_log2 = 16;
+    s->po.stop_rule = s->opts.stop_rule;
+    // time slice: about 2^28 combinations of each resident code per tick (a fraction of a
+    // millisecond of the whole GPU per code), so codes that arrive wait at most a few ticks
+    int rc = s->eng.init(s->opts.slots, stream, 1ull << 28, 0);
     if (rc != MD_OK) {
         if (s->own) cudaStreamDestroy(s->own);
         delete s;

@@ -94,3 +94,14 @@ def test_batch_workload_sample(B):
     for (G, n, k), di, wi in zip(codes, d, wits):
         ds, ws = single(B, G, n, k)
         assert di == ds and np.array_equal(wi, ws)
+
+
+def test_batch_per_matrix_bound(B):
+    codes = mixed_codes()
+    d0, w0, s0 = B.md_batch(codes)
+    d1, w1, s1 = B.md_batch(codes, B.md_options_init(stop_rule=1))
+    assert s1 == [B.MD_OK] * len(codes) and d1 == d0
+    assert all(np.array_equal(x, y) for x, y in zip(w0, w1))
+    for (G, n, k), di, wi in zip(codes, d1, w1):
+        res = O.bz(G, n, k, threads=8, stop_rule=1)
+        assert di == res.d and np.array_equal(wi, res.witness)

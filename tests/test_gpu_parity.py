@@ -276,3 +276,52 @@ def test_budget_and_max_stage(B):
     d, wit, info, levels = run_gpu(B, G, n, k, max_stage=3)
     res = O.bz(G, n, k, stop_after_g=3)
     assert info["complete"] == 0 and d == res.d and levels == expected_levels(res, n)
+
+
+@pytest.mark.parametrize("n,k,seed", [(80, 40, 121), (96, 48, 145), (96, 48, 154)])
+def test_mid_level_stop(B, n, k, seed):
+    """Codes whose minimum weight equals the lower bound of the previous stage and first
+    appears in the middle of a split level: once U <= L the kernel skips work ranked after
+    the level's best codeword.  Every record still equals the oracle's."""
+    G = I.random_code(n, k, seed)
+    res = O.bz(G, n, k, threads=THREADS)
+    _, info = assert_parity(B, G, n, k, res=res)
+    # with one warp per SM the level's work items run in many waves, so work handed out after
+    # the settling codeword is found is skipped
+    _, slow = assert_parity(B, G, n, k, res=res, threads_per_block=32, blocks_per_sm=1)
+    SKIPPED.append(slow["skipped_work"])
+
+
+SKIPPED = []
+
+
+def test_mid_level_stop_skipped_work():
+    """The skip happened for at least one of the codes above (timing-dependent per code)."""
+    assert SKIPPED and max(SKIPPED) > 0
+
+
+@pytest.mark.parametrize("n,k,seed", RANDOM_CASES)
+def test_random_codes_per_matrix_bound(B, n, k, seed):
+    """Stop rule 1 (per-matrix bound) against the oracle with the same rule: same levels,
+    stop and witness; d and witness also equal the Alg. 1 run's."""
+    rows = T.random_rows(n, k, seed)
+    G = T.pack(rows, n)
+    res = O.bz(G, n, k, threads=THREADS, stop_rule=1)
+    base = oracle_bz_cached(G, n, k, (n, k, seed))
+    assert (res.d, res.key) == (base.d, base.key)
+    assert_parity(B, G, n, k, res=res, stop_rule=1)
+
+
+@pytest.mark.parametrize("n,k,seed", [(64, 32, 1), (90, 40, 3), (48, 16, 5), (100, 33, 13)])
+def test_permuted_column_order(B, n, k, seed):
+    """perm_trials: the run on the chosen column order equals the oracle's run on the
+    permuted matrix, with the witness mapped back to the caller's columns; d is unchanged."""
+    from tests.test_perm_search import choose_order, permute, to_caller
+    G = I.random_code(n, k, seed) if seed != 13 else T.pack(T.random_rows(n, k, seed), n)
+    order, _ = choose_order(G, n, k, 12, 99 + seed)
+    res = O.bz(permute(G, n, k, order), n, k, threads=THREADS)
+    d, wit, info, levels = run_gpu(B, G, n, k, perm_trials=12, perm_seed=99 + seed)
+    assert d == res.d == O.bz(G, n, k, threads=THREADS).d
+    assert T.unpack(wit.reshape(1, -1)) == to_caller(T.unpack(res.witness.reshape(1, -1)), order, n)
+    assert (info["key_g"], info["key_j"], info["key_rank"]) == res.key
+    assert levels == expected_levels(res, n)

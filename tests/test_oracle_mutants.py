@@ -19,8 +19,8 @@ MUTANTS = {
     "colex_reset_off_by_one": ("for (int t = 0; t < i; t++) c[t] = t;", "for (int t = 0; t < i; t++) c[t] = t + (t > 0);"),
     "colex_rank_position": ("r += mdo_binomial(c[i], i + 1);", "r += mdo_binomial(c[i], i);"),
     "unrank_comparison": ("while (mdo_binomial(v, i) > rank) v--;", "while (mdo_binomial(v, i) >= rank && v > 0) v--;"),
-    "bound_drops_plus_one": ("int64_t t = (int64_t)g + 1 - (k - ranks[j]);", "int64_t t = (int64_t)g - (k - ranks[j]);"),
-    "bound_sign": ("int64_t t = (int64_t)g + 1 - (k - ranks[j]);", "int64_t t = (int64_t)g + 1 + (k - ranks[j]);"),
+    "bound_drops_plus_one": ("int64_t t = (int64_t)g + 1 - (k - kj);", "int64_t t = (int64_t)g - (k - kj);"),
+    "bound_sign": ("int64_t t = (int64_t)g + 1 - (k - kj);", "int64_t t = (int64_t)g + 1 + (k - kj);"),
     "stop_check_strict": ("if (L >= U) { stop = 1; break; }", "if (L > U) { stop = 1; break; }"),
     "no_per_matrix_check": ("if (L >= U) { stop = 1; break; }", "(void)0;"),
     "last_rank_not_first": ("if (w < J->minw) { J->minw = w; J->first = rank; }", "if (w <= J->minw) { J->minw = w; J->first = rank; }"),
@@ -31,6 +31,7 @@ MUTANTS = {
     "skip_last_gamma": ("        for (int j = 0; j < m; j++) {\n            int w; uint64_t first;", "        for (int j = 0; j < m - (m > 1); j++) {\n            int w; uint64_t first;"),
     "witness_drops_row": ("for (int i = 0; i < key_g; i++) xor_row(witness", "for (int i = 1; i < key_g; i++) xor_row(witness"),
     "info_set_not_greedy": ("for (int q = 0; q < nrem && r < k; q++) {\n            int col = remaining[q];", "for (int q = 0; q < nrem && r < k; q++) {\n            int col = remaining[nrem - 1 - q];"),
+    "per_matrix_bound_too_strong": ("L += set_bound(i <= j ? g : g - 1, k, ranks[i]);", "L += set_bound(g, k, ranks[i]);"),
     "partial_set_rank_off": ("            ranks[m++] = r;\n", "            ranks[m++] = r - (r > 1);\n"),
     "weight_ignores_column0": ("for (int i = 0; i < nw; i++) w += __builtin_popcountll(row[i]);", "for (int i = 0; i < nw; i++) w += __builtin_popcountll(row[i] & (i ? ~0ull : ~1ull));"),
 }

@@ -296,6 +296,36 @@ def test_bz_stop_rule_and_bound():
         assert len(res.levels) == res.nlevels
 
 
+@pytest.mark.parametrize("n,k,seed", [(12, 4, 1), (31, 10, 3), (48, 16, 4), (66, 12, 6), (40, 20, 11),
+                                      (57, 19, 12), (30, 10, 31), (45, 12, 32)])
+def test_bz_per_matrix_bound(n, k, seed):
+    """Stop rule 1 (after matrix j of stage g: matrices <= j have completed stage g, the others
+    stage g - 1) gives the same d and witness as Alg. 1 and brute force, runs a prefix of
+    Alg. 1's levels, and stops exactly where the per-matrix bound first reaches U."""
+    rows = T.random_rows(n, k, seed)
+    G = T.pack(rows, n)
+    a = O.bz(G, n, k)
+    b = O.bz(G, n, k, stop_rule=1)
+    d_bf, _ = O.bruteforce(G, n, k)
+    assert b.d == a.d == d_bf
+    assert b.key == a.key and np.array_equal(b.witness, a.witness)
+    assert b.levels == a.levels[:len(b.levels)]
+    check_bz_invariants(rows, n, k, b)
+    _, ranks = O.info_sets(G, n, k)
+    m = len(ranks)
+    bound = lambda g, kj: max(0, g + 1 - (k - kj))
+    U = None
+    stop_at = None
+    for rec in a.levels:
+        g, j = rec[0], rec[1]
+        U = rec[2] if U is None else min(U, rec[2])
+        Lj = sum(bound(g if i <= j else g - 1, ranks[i]) for i in range(m))
+        if Lj >= U:
+            stop_at = (g, j)
+            break
+    assert stop_at == b.stop
+
+
 def test_bz_partial_run_and_codeword_count():
     from paper_1911_08963_gb300 import inputs
     G, n, k = inputs.single_code("rand200x100")
