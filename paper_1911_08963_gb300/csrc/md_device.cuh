@@ -316,10 +316,13 @@ __device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, 
     // the completed stages' bound does not change during a level: the mid-level stop can only
     // apply once U has come down to it
     const int Lfix = c.L ? *(volatile const int *)c.L : -1;
+    // U as last read; the read for the next head check is issued before each pair walk so its
+    // latency hides behind the walk
+    int Upre = Usnap;
 
     for (long long it = 0; it < (long long)per_lane; it += NU) {
         // a lane whose next upper part starts above the rank that settles the run stops
-        if (remaining > 0 && Usnap <= Lfix && up.R > skip_above(c, U)) {
+        if (remaining > 0 && min(Usnap, Upre) <= Lfix && up.R > skip_above(c, U)) {
             if (c.skipped) atomicAdd(c.skipped, (unsigned long long)remaining);
             remaining = 0;
         }
@@ -366,10 +369,11 @@ __device__ __forceinline__ void split_chunk(const ChunkCtx &c, const MEntry &e, 
                 }
                 // heads are walked in rank order: once every lane's next rank lies above the
                 // rank that settles the run, the rest of this upper part's heads can go
-                if (__any_sync(kFull, Usnap <= Lfix) && __all_sync(kFull, !on || rmin > skip_above(c, U))) {
+                if (__any_sync(kFull, Upre <= Lfix) && __all_sync(kFull, !on || rmin > skip_above(c, U))) {
                     if (c.skipped && (threadIdx.x & 31) == 0) atomicAdd(c.skipped, 1ull);
                     break;
                 }
+                if (Lfix >= 0) Upre = (int)*(volatile const unsigned int *)U;
                 const int n2 = c3 * (c3 - 1) / 2;
                 walk_dispatch<W, WP, NU>(F, h2, T, n2, thr, c.base, best, rb);
             }
