@@ -98,6 +98,11 @@ typedef struct md_options {
                                  the last set, wins (earlier trial on ties).  0 or 1 = the given
                                  order.  Outputs stay in the caller's column order. */
     uint64_t perm_seed;
+    int tensor;               /* md_compute: 1 (default) = run large levels on the tensor cores
+                                 (tcgen05 MMA over +-1 encodings of the packed rows, exact
+                                 integer results); 0 = never; 2 = every level with g >= q + 1
+                                 (a test setting).  Results are identical for all. */
+    int tensor_head;          /* head size q of the tensor-core split (2 or 3); 0 = automatic */
 } md_options;
 
 /* Result details of the last md_compute on a handle. */

@@ -30,7 +30,8 @@ class md_options(ctypes.Structure):
                 ("threads_per_block", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("filter", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("cancel_flag", ctypes.POINTER(ctypes.c_int)),
                 ("batch_mode", ctypes.c_int), ("use_graph", ctypes.c_int), ("plan_horizon", ctypes.c_int),
-                ("stop_rule", ctypes.c_int), ("perm_trials", ctypes.c_int), ("perm_seed", ctypes.c_uint64)]
+                ("stop_rule", ctypes.c_int), ("perm_trials", ctypes.c_int), ("perm_seed", ctypes.c_uint64),
+                ("tensor", ctypes.c_int), ("tensor_head", ctypes.c_int)]
 
 
 class md_info(ctypes.Structure):

@@ -23,6 +23,7 @@ struct DevLayout {
     char *base = nullptr;
     size_t bytes = 0;
     std::vector<uint32_t *> rows, h2;
+    std::vector<unsigned char *> heads;     // tensor-core tables per matrix (null: none)
     unsigned long long *binom = nullptr;
     MEntry *mtab = nullptr;
     DevState *st = nullptr;
@@ -112,6 +113,8 @@ int setup_device(md_ctx *h) {
     po.chunk_log2 = h->opt.chunk_log2 > 0 ? h->opt.chunk_log2 : 20;
     po.filter = h->opt.filter;
     po.stop_rule = h->opt.stop_rule;
+    po.tensor = h->opt.tensor;
+    po.tensor_head = h->opt.tensor_head;
     h->g_limit = 0;
     for (int g = 1; g <= std::min(k, kMaxG); g++) {
         if (binom(k, g) >= kRankLimit) break;
@@ -128,13 +131,21 @@ int setup_device(md_ctx *h) {
             mtab_entries += h->plans.back().mtab.size();
         }
 
+    // head size of each matrix's tensor-core levels (0: it has none)
+    std::vector<int> tc_q(m, 0);
+    for (const LevelPlan &p : h->plans)
+        if (p.kind == KIND_TC) tc_q[p.j] = p.tc_q;
     size_t off = 0;
-    std::vector<size_t> rows_off(m), h2_off(m);
+    std::vector<size_t> rows_off(m), h2_off(m), heads_off(m, 0);
     for (int j = 0; j < m; j++) {
         rows_off[j] = off;
         off = align256(off + (size_t)k * c.gam[j].WP * 4);
         h2_off[j] = off;
         off = align256(off + (size_t)k * (k - 1) / 2 * c.gam[j].WP * 4 + 16);
+        if (tc_q[j]) {
+            heads_off[j] = off;
+            off = align256(off + tc_tables_bytes(k, tc_q[j], c.gam[j].W));
+        }
     }
     const size_t binom_off = off;
     off = align256(off + (size_t)(k + 1) * (k + 1) * 8);
@@ -160,9 +171,11 @@ int setup_device(md_ctx *h) {
     h->dev.bytes = off;
     h->dev.rows.resize(m);
     h->dev.h2.resize(m);
+    h->dev.heads.assign(m, nullptr);
     for (int j = 0; j < m; j++) {
         h->dev.rows[j] = (uint32_t *)(h->dev.base + rows_off[j]);
         h->dev.h2[j] = (uint32_t *)(h->dev.base + h2_off[j]);
+        if (tc_q[j]) h->dev.heads[j] = (unsigned char *)(h->dev.base + heads_off[j]);
     }
     h->dev.binom = (unsigned long long *)(h->dev.base + binom_off);
     h->dev.mtab = (MEntry *)(h->dev.base + mtab_off);
@@ -184,9 +197,16 @@ int setup_device(md_ctx *h) {
              cudaSuccess;
         if (ok) ok = launch_h2_build(h->dev.rows[j], h->dev.h2[j], k, c.gam[j].WP, s) == 0;
     }
+    int head_tables = 0;
+    for (int j = 0; ok && j < m; j++)
+        if (tc_q[j]) {
+            ok = launch_tc_tables(h->dev.rows[j], h->dev.binom, k, tc_q[j], c.gam[j].W, c.gam[j].WP,
+                                  h->dev.heads[j], s) == 0;
+            head_tables++;
+        }
     if (ok) ok = cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) { cudaGetLastError(); free_device(h); return MD_ECUDA; }
-    h->setup_launches = m;
+    h->setup_launches = m + head_tables;
     h->setup_h2d = tb.size() * 8 + all.size() * sizeof(MEntry);
     for (int j = 0; j < m; j++) h->setup_h2d += c.gam[j].packed.size() * 4;
     h->dev_ready = true;
@@ -260,6 +280,7 @@ int md_options_init(md_options *opt) {
     opt->chunk_log2 = 20;
     opt->filter = 1;
     opt->use_graph = 1;
+    opt->tensor = 1;
     return MD_OK;
 }
 
@@ -367,10 +388,17 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
         for (int j = 0; j < m && !err; j++) {
             const int level = (g - 1) * m + j;
             const LevelPlan &p = h->plans[level];
-            LaunchCfg L = launch_cfg(h, p);
-            LevelArgs a = level_args(h, p, level, L.h2s);
             cudaEventRecord(h->lev_ev[nlev_ev], s);
-            err |= launch_level(a, p.kind, c.gam[p.j].W, c.gam[p.j].WP, L.blocks, L.threads, L.smem, s) != 0;
+            LevelArgs a;
+            if (p.kind == KIND_TC) {
+                a = level_args(h, p, level, false);
+                err |= launch_tc_level(h->dev.heads[p.j], h->dev.rows[p.j], h->dev.binom, h->dev.st, k, p.g, p.tc_q,
+                                       p.base, level, c.gam[p.j].W, c.gam[p.j].WP, 1, h->sms, s) != 0;
+            } else {
+                LaunchCfg L = launch_cfg(h, p);
+                a = level_args(h, p, level, L.h2s);
+                err |= launch_level(a, p.kind, c.gam[p.j].W, c.gam[p.j].WP, L.blocks, L.threads, L.smem, s) != 0;
+            }
             cudaEventRecord(h->lev_ev[nlev_ev + 1], s);
             nlev_ev += 2;
             err |= launch_finalize(a, s) != 0;
@@ -400,7 +428,7 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
     if (cudaMemcpy(h->host_state, h->dev.st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) return MD_ECUDA;
     d2h += sizeof(DevState);
     const DevState &st = *h->host_state;
-    if (st.error) return MD_EINTERNAL;
+    if (st.error) return st.error == MD_ETIMEOUT ? MD_ETIMEOUT : MD_EINTERNAL;
     // complete: L >= U was reached, or every stage up to g = k ran (Alg. 1's loop bound)
     stopped = st.stop != 0 || (status == MD_OK && st.last_level == k * m - 1);
 

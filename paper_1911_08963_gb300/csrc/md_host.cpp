@@ -360,6 +360,21 @@ LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o) {
         p.L_after = j == (int)c.gam.size() - 1 ? lower_bound_after(c, g) : -1;
     }
     p.fmax8 = o.filter == 1 ? gm.fmax8 : filter_thresholds(gm, o.filter);
+    if (o.tensor && g <= kMaxG) {
+        // tensor-core level: head (c_1..c_q) x tail products, see md_tc.cu
+        const int q = o.tensor_head ? o.tensor_head : tc_auto_head(k, gm.W);
+        const int v = g - q - 1;
+        bool use = false;
+        if ((q == 2 || q == 3) && q < k && v >= 0 && v <= tc_max_upper())
+            use = o.tensor == 2 || (v >= 1 && p.count >= (1ull << 28));
+        if (use) {
+            p.kind = KIND_TC;
+            p.tc_q = q;
+            p.v = v;
+            p.nchunks = tc_level_items(k, g, q, gm.W);
+            return p;
+        }
+    }
     const uint64_t target_full = 1ull << std::max(8, std::min(30, o.chunk_log2));
     // keep at least ~64 work items per SM-sized slice of the level
     const uint64_t target = std::max<uint64_t>(1ull << 10, std::min<uint64_t>(target_full, p.count / (152ull * 64)));

@@ -80,7 +80,7 @@ struct MEntry {
     uint32_t per_lane;      // upper parts per lane in one work item
 };
 
-enum KernelKind : int { KIND_SIMPLE = 0, KIND_SPLIT2 = 2, KIND_SPLIT3 = 3 };
+enum KernelKind : int { KIND_SIMPLE = 0, KIND_SPLIT2 = 2, KIND_SPLIT3 = 3, KIND_TC = 4 };
 
 struct LevelPlan {
     int g = 0, j = 0;
@@ -96,6 +96,7 @@ struct LevelPlan {
     uint64_t nchunks = 0;
     uint64_t per_chunk = 0;         // kind 0: ranks per lane
     std::vector<MEntry> mtab;       // kinds 2, 3
+    int tc_q = 0;                   // kind 4: head size q (tail = the other g - q elements)
 };
 
 struct PlanOptions {
@@ -104,7 +105,16 @@ struct PlanOptions {
     uint64_t perm_seed = 0;
     int chunk_log2 = 20;
     int filter = 1;                 // 0 = never, 1 = when it pays, 2 = always
+    int tensor = 0;                 // 0 = never, 1 = large levels, 2 = every level it can run
+    int tensor_head = 0;            // q for the tensor-core levels (0 = automatic)
 };
+
+// ---- tensor-core levels (md_tc.cu) ----
+size_t tc_tables_bytes(int k, int q, int W);  // head table of one matrix
+int tc_smem_bytes(int k, int W, int WP);
+uint64_t tc_level_items(int k, int g, int q, int W);
+int tc_auto_head(int k, int W);     // q used when PlanOptions::tensor_head is 0
+int tc_max_upper();                 // largest g - q - 1 the tensor-core kernel handles
 
 LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o);
 
@@ -208,6 +218,12 @@ double estimate_work(const Code &c, int *d_est, int *g_stop);
 
 // Launchers (md_kernels.cu).  Return cudaError_t as int.
 int launch_h2_build(const uint32_t *rows, uint32_t *h2, int k, int WP, void *stream);
+// Tables of Gamma_j for its tensor-core levels (tc_tables_bytes(k, q, W) bytes, 16-byte aligned).
+int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, int k, int q, int W, int WP,
+                     unsigned char *tables, void *stream);
+// One tensor-core level: `blocks` persistent blocks (one per SM), work items from st->ctr[level].
+int launch_tc_level(const unsigned char *tables, const uint32_t *rows, const unsigned long long *binom_d, DevState *st,
+                    int k, int g, int q, int base, int level, int W, int WP, int check_stop, int blocks, void *stream);
 int launch_level(const LevelArgs &a, int kind, int W, int WP, int blocks, int threads, size_t smem,
                  void *stream);
 int launch_finalize(const LevelArgs &a, void *stream);

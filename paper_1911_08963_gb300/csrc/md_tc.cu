@@ -1,0 +1,872 @@
+// md_tc.cu -- one level (g, j) of the enumeration on the fifth-generation tensor cores.
+//
+// The weight of a sum of g rows of Gamma_j is base + popcount(S), S the XOR of their packed
+// rows.  Mapping every packed bit b to the sign (-1)^b turns the popcount into an inner
+// product: for packed vectors x, y of K = 32 W bits,  <sign x, sign y> = K - 2 popcount(x ^ y).
+//
+// A combination c_1 < ... < c_g is split into a head (c_1..c_q) and a tail (c_{q+1}..c_g)
+// with smallest tail element s = c_{q+1}.  For one s the admissible heads are exactly the
+// q-subsets of [0, s), i.e. the first C(s, q) heads in colex order, and every (tail, head)
+// pair of that s is a combination.  So the weights of all combinations with a given s form
+// one dense product D = A B^T, A = signs of the tail sums, B = signs of the head sums: the
+// left/right combination split of Section 2.2.1 taken all the way to a matrix product.  Its
+// colex rank is (head index) + sum_{i > q} C(c_i, i), so within one tail the first column
+// holding a row's best weight is that tail's smallest rank of it.
+//
+//   * Heads: a table of the C(k, q) head sums as e4m3 signs (+1.0 = 0x38, -1.0 = 0xB8), in
+//     256-row slices of 8-row x 16-byte core matrices (the K-major operand layout without
+//     swizzle), built once per matrix and copied slice by slice into shared memory with bulk
+//     copies (cp.async.bulk, completion on an mbarrier).
+//   * Tails: eight producer warps, two threads per tile row (each owns half of the packed
+//     words); a thread walks its own run of consecutive tails in colex order, keeping its
+//     words of the tail sum in registers, and writes the e4m3 signs of those words: two
+//     16-byte stores per packed word.  A colex step moves a run of consecutive elements
+//     o0..o0+m: they leave, s+1..s+m and o0+m+1 enter, which prefix XORs of the rows give in
+//     five lookups whatever m is (usually m = 0: one XOR with the difference of two adjacent
+//     rows).  The rows, their adjacent differences and prefix XORs sit in shared memory
+//     word-major, so the 32 lanes' reads spread over the banks.
+//   * A work item is a block of up to 128 T tails (T tiles, kept in shared memory, two sets
+//     so the producers fill one while the other is in use) times a group of up to 16 head
+//     slices of the same s: every tail tile is multiplied with each slice of the group, so
+//     generating it costs little per codeword, and each slice is fetched once for T tiles.
+//   * One thread issues tcgen05.mma kind::f8f6f4 (M = 128 tails, N <= 256 heads, one
+//     instruction per 32 packed bits); D accumulates in fp32 in tensor memory (exact, |D| <=
+//     256), two accumulators of 256 columns so the next product overlaps the epilogue.
+//   * Eight epilogue warps (two per tensor-memory lane quarter, one per half of the columns)
+//     read D with tcgen05.ld.red, which also returns each lane's maximum over the columns
+//     it loads, so no per-element arithmetic is left; a row reaching
+//     K - 2 (min(U, best) - base) is resolved to (weight, first rank) and published with
+//     atomicMin, as in the other level kernels.
+//   * One scheduler thread takes work items (s, head slices, run of tails) from the level's
+//     atomic counter, applies the mid-level stop, and passes them on through a ring in shared
+//     memory.
+// Every wait is bounded by the global timer; on expiry the block records MD_ETIMEOUT in the
+// state, waits (bounded) for its own tensor-core work, frees its tensor memory and returns.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "md_device.cuh"
+#include "md_internal.h"
+
+namespace mdl {
+
+namespace {
+
+using namespace dev;
+
+constexpr int kTcM = 128;                  // tails per tile (tensor-memory lanes)
+constexpr int kTcN = 256;                  // heads per slice (accumulator columns)
+constexpr int kEpiWarps = 8;               // warps 0-7
+constexpr int kProdWarp0 = 8;              // warps 8-15
+constexpr int kProdWarps = 8;
+constexpr int kMmaWarp = 16;
+constexpr int kSchedWarp = 17;
+constexpr int kTcWarps = 18;
+constexpr int kTcThreads = kTcWarps * 32;
+constexpr int kRing = 8;                   // work items between the scheduler and the others
+constexpr int kItemReaders = kEpiWarps + kProdWarps + 1;   // warps that take each ring entry
+constexpr uint32_t kTmemCols = 512;
+constexpr unsigned long long kWaitNs = 4000000000ull;
+constexpr int kMaxV = 10;                  // upper elements of a tail (g - q - 1) handled
+
+constexpr int kGroup = 16;                 // head slices per work item
+
+// Tail tiles per set (two sets), as shared memory allows for the row width.
+__host__ __device__ constexpr int tc_tiles_per_set(int W) { return W <= 2 ? 8 : W <= 4 ? 4 : W <= 6 ? 2 : 1; }
+
+template <int W>
+struct TcCfg {
+    static constexpr int kTiles = tc_tiles_per_set(W);
+    static constexpr int kATile = kTcM * 32 * W;           // bytes of one tail tile
+    static constexpr int kBTile = kTcN * 32 * W;           // bytes of one head slice
+    static constexpr int kSbo = 256 * W;                   // bytes per 8-row group
+};
+
+struct TcItem {
+    unsigned long long t0;                 // first tail (colex index among the tails of s)
+    int s;                                 // smallest tail element
+    int sl0;                               // first head slice (heads sl0 * 256 ...)
+    int nsl;                               // head slices in the item
+    int nb;                                // heads of s: C(s, q)
+    int nt;                                // tails in the item
+    int na;                                // tail tiles: ceil(nt / 128); tile a row r = tail t0 + r na + a
+    int u;                                 // U when the item was handed out
+    int end;                               // 1: the level has no more items
+};
+
+// Heads of slice sl that belong to s (the MMA N covers them rounded up to 16).
+__device__ __forceinline__ int slice_heads(const TcItem &it, int sl) { return min(kTcN, it.nb - sl * kTcN); }
+
+struct TcShared {
+    unsigned long long afull[2];           // producers -> MMA: tail set written (8 warp arrivals)
+    unsigned long long afree[2];           // MMA -> producers: products reading the set done
+    unsigned long long mdone[2];           // MMA -> epilogue: accumulator complete
+    unsigned long long tfree[2];           // epilogue -> MMA: accumulator read (8 arrivals)
+    unsigned long long bfull[2];           // head slice landed (transaction count)
+    unsigned long long bfree[2];           // MMA -> MMA: products reading the slice complete
+    unsigned long long ifull[kRing];       // scheduler -> readers
+    unsigned long long ifree[kRing];       // readers -> scheduler (17 warp arrivals)
+    TcItem ring[kRing];
+    unsigned long long cum[kMaxN + 1];     // work items before s
+    uint32_t taddr;
+    int abort;
+    int stop;
+};
+
+__host__ __device__ constexpr int align_up(int x, int a) { return (x + a - 1) / a * a; }
+constexpr int kHdrBytes = align_up((int)sizeof(TcShared), 1024);
+
+// ------------------------------------------------------------------ PTX wrappers ----
+__device__ __forceinline__ uint32_t saddr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// One try_wait (the hardware may hold the thread for a short, system-defined time).
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of parity `parity` to complete.  False once the block aborts or the wait
+// exceeds kWaitNs (which aborts the block).
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    const uint64_t t0 = gtimer();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > kWaitNs) {
+            *abort_flag = 1;
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    return mbar_test(bar, parity) || mbar_wait_slow(bar, parity, abort_flag);
+}
+
+// All lanes of a warp wait; the outcome is made warp-uniform (the warp's later
+// .sync.aligned instructions need every lane).
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag) {
+    const bool ok = mbar_wait(bar, parity, abort_flag);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// The same without the abort flag (draining after an abort), bounded.
+__device__ __forceinline__ void mbar_drain(uint32_t bar, uint32_t parity) {
+    const uint64_t t0 = gtimer();
+    while (!mbar_test(bar, parity) && gtimer() - t0 < kWaitNs) {
+    }
+}
+
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tc_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+}
+
+// Shared-memory operand descriptor: K-major, no swizzle; lbo = byte step between core
+// matrices along K, sbo = byte step between 8-row groups; bits 46-48 = 0b001.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Instruction descriptor, kind::f8f6f4: fp32 accumulator, A and B e4m3, both K-major, M = 128.
+__device__ __forceinline__ uint32_t idesc_e4m3(int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 32 consecutive accumulator columns of this warp's 32 lanes; the values are valid after a
+// tmem_wait that takes them as operands (so no use moves above the wait).
+#define MDL_R8(a, i) "=r"(a[i]), "=r"(a[i + 1]), "=r"(a[i + 2]), "=r"(a[i + 3]), "=r"(a[i + 4]), "=r"(a[i + 5]), \
+                     "=r"(a[i + 6]), "=r"(a[i + 7])
+#define MDL_P8(a, i) "+r"(a[i]), "+r"(a[i + 1]), "+r"(a[i + 2]), "+r"(a[i + 3]), "+r"(a[i + 4]), "+r"(a[i + 5]), \
+                     "+r"(a[i + 6]), "+r"(a[i + 7])
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : MDL_R8(v, 0), MDL_R8(v, 8), MDL_R8(v, 16), MDL_R8(v, 24)
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait(uint32_t (&v)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : MDL_P8(v, 0), MDL_P8(v, 8), MDL_P8(v, 16), MDL_P8(v, 24)::"memory");
+}
+__device__ __forceinline__ void tmem_wait2(uint32_t (&v)[32], uint32_t (&u)[32]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : MDL_P8(v, 0), MDL_P8(v, 8), MDL_P8(v, 16), MDL_P8(v, 24), MDL_P8(u, 0), MDL_P8(u, 8),
+                   MDL_P8(u, 16), MDL_P8(u, 24)::"memory");
+}
+#define MDL_F8(a, i) "=f"(a[i]), "=f"(a[i + 1]), "=f"(a[i + 2]), "=f"(a[i + 3]), "=f"(a[i + 4]), "=f"(a[i + 5]), \
+                     "=f"(a[i + 6]), "=f"(a[i + 7])
+#define MDL_G8(a, i) "+f"(a[i]), "+f"(a[i + 1]), "+f"(a[i + 2]), "+f"(a[i + 3]), "+f"(a[i + 4]), "+f"(a[i + 5]), \
+                     "+f"(a[i + 6]), "+f"(a[i + 7])
+// As tmem_ld32, and `red` = the maximum of the 32 values (tcgen05.ld.red, sm_103a).
+__device__ __forceinline__ void tmem_ldmax32(uint32_t taddr, float (&v)[32], float &red) {
+    asm volatile(
+        "tcgen05.ld.red.sync.aligned.32x32b.x32.max.f32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, %32, [%33];"
+        : MDL_F8(v, 0), MDL_F8(v, 8), MDL_F8(v, 16), MDL_F8(v, 24), "=f"(red)
+        : "r"(taddr));
+}
+// Wait for two reducing loads; every register they write is an operand, so none is reused
+// before the data lands.
+__device__ __forceinline__ void tmem_wait_red2(float (&v)[32], float &rv, float (&u)[32], float &ru) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : MDL_G8(v, 0), MDL_G8(v, 8), MDL_G8(v, 16), MDL_G8(v, 24), MDL_G8(u, 0), MDL_G8(u, 8),
+                   MDL_G8(u, 16), MDL_G8(u, 24), "+f"(rv), "+f"(ru)::"memory");
+}
+#undef MDL_F8
+#undef MDL_G8
+#undef MDL_R8
+#undef MDL_P8
+
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// Maximum of the first `valid` (all 32 when valid >= 32) accumulator values of a chunk, as a
+// shallow tree: four independent chains of three-input maxima.
+__device__ __forceinline__ float chunk_max(const uint32_t (&v)[32], int valid) {
+    if (valid >= 32) {
+        float m[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) m[j] = fmaxf(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+#pragma unroll
+        for (int i = 8; i < 32; i += 8)
+#pragma unroll
+            for (int j = 0; j < 4; j++) m[j] = fmax3(m[j], __uint_as_float(v[i + 2 * j]), __uint_as_float(v[i + 2 * j + 1]));
+        return fmax3(m[0], m[1], fmaxf(m[2], m[3]));
+    }
+    float m = -1e30f;
+#pragma unroll
+    for (int i = 0; i < 32; i++)
+        if (i < valid) m = fmaxf(m, __uint_as_float(v[i]));
+    return m;
+}
+
+// ---------------------------------------------------------------- sign encoding ----
+// The 32 sign bytes of packed word x (bit i -> byte i) as two 16-byte vectors: bit 7 of a
+// byte is its bit (the product places bit i of a nibble at bit 7 + 8 i -- the partial
+// products occupy disjoint bit positions, so there are no carries -- and the mask keeps
+// those bits); the rest is `base`: 0x38383838 gives the e4m3 values 0x38 (+1.0) and 0xB8
+// (-1.0), 0 only the sign bits (the part that is linear over XOR).
+__device__ __forceinline__ void sign_word(uint32_t x, uint32_t base, uint4 &lo, uint4 &hi) {
+    auto sb = [&](uint32_t nib) { return ((nib * 0x10204080u) & 0x80808080u) | base; };
+    lo = make_uint4(sb(x & 15u), sb((x >> 4) & 15u), sb((x >> 8) & 15u), sb((x >> 12) & 15u));
+    hi = make_uint4(sb((x >> 16) & 15u), sb((x >> 20) & 15u), sb((x >> 24) & 15u), sb(x >> 28));
+}
+
+// ------------------------------------------------------------------- tail walking ----
+struct TcArgs {
+    const unsigned char *heads;            // head slices (launch_tc_tables)
+    const uint32_t *rows;                  // k x WP packed rows of Gamma_j
+    const unsigned long long *binom;       // (k + 1) x (k + 1)
+    DevState *st;
+    int k, g, q, base, level, WP, tiles, check_stop;   // tiles: tail tiles per set
+};
+
+__device__ __forceinline__ unsigned long long C(const TcArgs &a, int n, int r) {
+    return (r < 0 || n < r) ? 0ull : __ldg(a.binom + (size_t)n * (a.k + 1) + r);
+}
+
+// Largest x in [lo, hi] with C(x, i) <= t (C(lo, i) <= t holds).
+__device__ __forceinline__ int colex_digit(const TcArgs &a, int lo, int hi, int i, unsigned long long t) {
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (C(a, mid, i) <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Tail index t (colex among the v-subsets of [s + 1, k)) -> its elements o[0..v), in registers.
+__device__ __forceinline__ void tail_unrank(const TcArgs &a, int s, int v, unsigned long long t, int (&o)[kMaxV]) {
+    int top = a.k - 2 - s;
+#pragma unroll
+    for (int i = kMaxV; i >= 1; i--) {
+        if (i <= v) {
+            const int x = colex_digit(a, i - 1, top, i, t);
+            o[i - 1] = x + s + 1;
+            t -= C(a, x, i);
+            top = x - 1;
+        }
+    }
+}
+
+// Rank contribution of the tail with index t: C(s, q + 1) + sum_i C(o_i, q + 2 + i).
+__device__ __forceinline__ unsigned long long tail_rank_at(const TcArgs &a, int s, unsigned long long t) {
+    const int v = a.g - a.q - 1;
+    int top = a.k - 2 - s;
+    unsigned long long r = C(a, s, a.q + 1);
+    for (int i = v; i >= 1; i--) {
+        const int x = colex_digit(a, i - 1, top, i, t);
+        t -= C(a, x, i);
+        top = x - 1;
+        r += C(a, x + s + 1, a.q + 1 + i);
+    }
+    return r;
+}
+
+// Items of s: groups of up to kGroup head slices x runs of 128 * tiles tails.
+__device__ __forceinline__ unsigned long long items_of(const TcArgs &a, int s) {
+    const int v = a.g - a.q - 1;
+    if (s < a.q || s > a.k - 1 - v) return 0;
+    const unsigned long long nb = C(a, s, a.q), nt = C(a, a.k - 1 - s, v);
+    const unsigned long long per = (unsigned long long)kTcM * a.tiles;
+    const unsigned long long nsl = (nb + kTcN - 1) / kTcN;
+    return ((nsl + kGroup - 1) / kGroup) * ((nt + per - 1) / per);
+}
+
+// S ^= the packed words [w0, w0 + NW) of row x of a word-major table (k rows).
+template <int NW>
+__device__ __forceinline__ void xor_words(uint32_t (&S)[NW], const uint32_t *tab, int k, int x, int w0, int W) {
+#pragma unroll
+    for (int i = 0; i < NW; i++)
+        if (w0 + i < W) S[i] ^= tab[(w0 + i) * k + x];
+}
+
+// ------------------------------------------------------------------------ kernel ----
+template <int W>
+__global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
+    using Cfg = TcCfg<W>;
+    constexpr int T = Cfg::kTiles;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    TcShared &sh = *reinterpret_cast<TcShared *>(smem);
+    // word-major tables: rT[w * k + x] = word w of row x, dT[w * k + x] = that of row x ^ row x+1,
+    // pX[w * (k + 1) + x] = that of row 0 ^ ... ^ row x-1
+    uint32_t *rT = reinterpret_cast<uint32_t *>(smem + kHdrBytes);
+    uint32_t *dT = rT + W * a.k;
+    uint32_t *pX = dT + W * a.k;
+    unsigned char *Atile = smem + kHdrBytes + align_up((3 * a.k + 1) * W * 4, 1024);   // [2][T] tiles
+    unsigned char *Btile = Atile + 2 * T * Cfg::kATile;                                // [2] slices
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    DevState *st = a.st;
+    const int k = a.k, q = a.q, v = a.g - a.q - 1;
+    volatile int *abort_flag = &sh.abort;
+
+    if (threadIdx.x == 0) {
+        sh.abort = 0;
+        sh.stop = a.check_stop ? *(volatile int *)&st->stop : 0;
+        for (int i = 0; i < 2; i++) {
+            mbar_init(saddr(&sh.afull[i]), kProdWarps);
+            mbar_init(saddr(&sh.afree[i]), 1);
+            mbar_init(saddr(&sh.mdone[i]), 1);
+            mbar_init(saddr(&sh.tfree[i]), kEpiWarps);
+            mbar_init(saddr(&sh.bfull[i]), 1);
+            mbar_init(saddr(&sh.bfree[i]), 1);
+        }
+        for (int i = 0; i < kRing; i++) {
+            mbar_init(saddr(&sh.ifull[i]), 1);
+            mbar_init(saddr(&sh.ifree[i]), kItemReaders);
+        }
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < k * W; i += blockDim.x) {
+        const int w = i / k, x = i % k;
+        const uint32_t y = __ldg(a.rows + x * a.WP + w);
+        rT[i] = y;
+        dT[i] = x + 1 < k ? y ^ __ldg(a.rows + (x + 1) * a.WP + w) : 0u;
+    }
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        uint32_t acc = 0;
+        for (int x = 0; x <= k; x++) {
+            pX[w * (k + 1) + x] = acc;
+            if (x < k) acc ^= __ldg(a.rows + x * a.WP + w);
+        }
+    }
+    for (int s = threadIdx.x; s < k; s += blockDim.x) sh.cum[s + 1] = items_of(a, s);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sh.cum[0] = 0;
+        for (int s = 0; s < k; s++) sh.cum[s + 1] += sh.cum[s];
+    }
+    __syncthreads();
+    if (sh.stop) return;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&sh.taddr)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = sh.taddr;
+
+    if (warp == kSchedWarp) {
+        // ------------------------------------------------------------ scheduler ----
+        if (lane == 0) {
+            const unsigned long long total = sh.cum[k];
+            const unsigned long long per = (unsigned long long)kTcM * T;
+            for (long long n = 0;; n++) {
+                const int slot = (int)(n % kRing);
+                const unsigned use = (unsigned)(n / kRing);
+                if (use >= 1 && !mbar_wait(saddr(&sh.ifree[slot]), (use - 1) & 1, abort_flag)) break;
+                TcItem it{};
+                for (;;) {
+                    const unsigned long long idx = atomicAdd(&st->ctr[a.level], 1ull);
+                    if (idx >= total) { it.end = 1; break; }
+                    int lo = 0, hi = k - 1;                    // last s with cum[s] <= idx
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (sh.cum[mid] <= idx) lo = mid; else hi = mid - 1;
+                    }
+                    const int s = lo;
+                    const unsigned long long local = idx - sh.cum[s];
+                    const unsigned long long nb = C(a, s, q);
+                    const unsigned long long nsl = (nb + kTcN - 1) / kTcN;
+                    const unsigned long long ngr = (nsl + kGroup - 1) / kGroup;
+                    const unsigned long long grp = local % ngr, tblock = local / ngr;
+                    it.s = s;
+                    it.nb = (int)nb;
+                    it.sl0 = (int)(grp * kGroup);
+                    it.nsl = (int)min((unsigned long long)kGroup, nsl - grp * kGroup);
+                    it.t0 = tblock * per;
+                    it.nt = (int)min(per, C(a, k - 1 - s, v) - it.t0);
+                    it.na = (it.nt + kTcM - 1) / kTcM;
+                    const int U = (int)*(volatile unsigned int *)&st->U;
+                    it.u = U;
+                    // mid-level stop: once U <= L this level holds the answer's weight, and an
+                    // item whose smallest rank lies above the best rank of that weight can go
+                    if (a.check_stop && U <= *(volatile int *)&st->L) {
+                        const unsigned long long key = *(volatile unsigned long long *)&st->key[a.level];
+                        if (key != kNoKey && (int)(key >> kRankBits) == U &&
+                            (unsigned long long)it.sl0 * kTcN + tail_rank_at(a, s, it.t0) > (key & (kRankLimit - 1))) {
+                            atomicAdd(&st->skipped, 1ull);
+                            continue;
+                        }
+                    }
+                    break;
+                }
+                sh.ring[slot] = it;
+                mbar_arrive(saddr(&sh.ifull[slot]));
+                if (it.end) break;
+            }
+        }
+    } else if (warp == kMmaWarp) {
+        // ------------------------------------------------- MMA issue and head slices ----
+        if (lane == 0) {
+            long long n = 0;                               // ring entries taken
+            bool ok = true;
+            auto take = [&](TcItem &it) -> bool {
+                const int slot = (int)(n % kRing);
+                if (!mbar_wait(saddr(&sh.ifull[slot]), (unsigned)(n / kRing) & 1, abort_flag)) return false;
+                it = sh.ring[slot];
+                mbar_arrive(saddr(&sh.ifree[slot]));
+                n++;
+                return true;
+            };
+            int pend_buf = -1;                             // head slice copy not yet waited for
+            unsigned pend_parity = 0;
+            auto load_slice = [&](const TcItem &it, int sl, long long step) {
+                const int buf = (int)(step & 1);
+                const int npad = (slice_heads(it, sl) + 15) & ~15;
+                const uint32_t bytes = (uint32_t)(npad / 8) * Cfg::kSbo;
+                const unsigned char *src = a.heads + (size_t)sl * Cfg::kBTile;
+                mbar_expect_tx(saddr(&sh.bfull[buf]), bytes);
+                bulk_g2s(saddr(Btile + buf * Cfg::kBTile), src, bytes, saddr(&sh.bfull[buf]));
+                pend_buf = buf;
+                pend_parity = (unsigned)(step >> 1) & 1;
+            };
+            TcItem cur{}, nxt{};
+            unsigned u = 0;                                // accumulator uses
+            long long step = 0;                            // head slices multiplied
+            long long j = 0;                               // items
+            int last_acc = -1;
+            unsigned last_parity = 0;
+            ok = take(cur);
+            if (ok && !cur.end) load_slice(cur, cur.sl0, 0);
+            while (ok && !cur.end) {
+                const int set = (int)(j & 1);
+                if (!mbar_wait(saddr(&sh.afull[set]), (unsigned)(j >> 1) & 1, abort_flag)) { ok = false; break; }
+                nxt.end = 1;
+                for (int sl = 0; sl < cur.nsl && ok; sl++, step++) {
+                    const int bb = (int)(step & 1);
+                    if (!mbar_wait(saddr(&sh.bfull[bb]), (unsigned)(step >> 1) & 1, abort_flag)) { ok = false; break; }
+                    if (pend_buf == bb) pend_buf = -1;
+                    const uint32_t idesc = idesc_e4m3((slice_heads(cur, cur.sl0 + sl) + 15) & ~15);
+                    const uint32_t bbase = saddr(Btile + bb * Cfg::kBTile);
+                    for (int t = 0; t < cur.na; t++) {
+                        const int acc = (int)(u & 1);
+                        if (u >= 2 && !mbar_wait(saddr(&sh.tfree[acc]), ((u >> 1) - 1) & 1, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_after();
+                        const uint32_t abase = saddr(Atile + (set * T + t) * Cfg::kATile);
+                        const uint32_t d = tmem + (uint32_t)(acc * kTcN);
+#pragma unroll
+                        for (int w = 0; w < W; w++)
+                            mma_e4m3(d, smem_desc(abase + 256u * w, 128u, Cfg::kSbo),
+                                     smem_desc(bbase + 256u * w, 128u, Cfg::kSbo), idesc, w > 0 ? 1u : 0u);
+                        mma_commit(saddr(&sh.mdone[acc]));
+                        last_acc = acc;
+                        last_parity = (u >> 1) & 1;
+                        u++;
+                    }
+                    if (!ok) break;
+                    mma_commit(saddr(&sh.bfree[bb]));
+                    // the next slice (of this item or the next) goes into the other buffer once
+                    // the products of the slice before this one are done with it
+                    const TcItem *ni = &cur;
+                    int nsl_idx = cur.sl0 + sl + 1;
+                    if (sl + 1 == cur.nsl) {
+                        if (!take(nxt)) { ok = false; break; }
+                        ni = &nxt;
+                        nsl_idx = nxt.sl0;
+                    }
+                    if (!ni->end) {
+                        if (step >= 1 &&
+                            !mbar_wait(saddr(&sh.bfree[(step + 1) & 1]), (unsigned)((step - 1) >> 1) & 1, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        load_slice(*ni, nsl_idx, step + 1);
+                    }
+                }
+                if (!ok) break;
+                mma_commit(saddr(&sh.afree[set]));
+                cur = nxt;
+                j++;
+            }
+            if (!ok) {
+                if (last_acc >= 0) mbar_drain(saddr(&sh.mdone[last_acc]), last_parity);
+                if (pend_buf >= 0) mbar_drain(saddr(&sh.bfull[pend_buf]), pend_parity);
+            }
+        }
+    } else if (warp >= kProdWarp0) {
+        // ------------------------------------------------------------ producers ----
+        // two threads per tile row: part h owns packed words [h * NW, h * NW + NW)
+        constexpr int NW = (W + 1) / 2;
+        const int pw = warp - kProdWarp0;
+        const int part = pw >> 2;
+        const int r = (pw & 3) * 32 + lane;                // tile row
+        const int w0 = part * NW;
+        long long n = 0, j = 0;
+        int o[kMaxV];                                      // upper elements of the current tail
+#pragma unroll
+        for (int i = 0; i < kMaxV; i++) o[i] = 0;
+        uint32_t Sx[NW];                                   // this thread's words of the tail sum
+        unsigned char *rowp0 = Atile + (r >> 3) * Cfg::kSbo + (r & 7) * 16 + w0 * 256;
+        for (;;) {
+            const int slot = (int)(n % kRing);
+            if (!warp_wait(saddr(&sh.ifull[slot]), (unsigned)(n / kRing) & 1, abort_flag)) break;
+            const TcItem it = sh.ring[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(saddr(&sh.ifree[slot]));
+            n++;
+            if (it.end) break;
+            const int set = (int)(j & 1);
+            if (j >= 2 && !warp_wait(saddr(&sh.afree[set]), (unsigned)((j >> 1) - 1) & 1, abort_flag)) break;
+            const int first = r * it.na;
+            const int cnt = max(0, min(it.na, it.nt - first));
+#pragma unroll
+            for (int i = 0; i < NW; i++) Sx[i] = 0;
+            if (cnt > 0) {
+                tail_unrank(a, it.s, v, it.t0 + (unsigned long long)first, o);
+                xor_words<NW>(Sx, rT, k, it.s, w0, W);
+#pragma unroll
+                for (int i = 0; i < kMaxV; i++)
+                    if (i < v) xor_words<NW>(Sx, rT, k, o[i], w0, W);
+            }
+            for (int t = 0; t < it.na; t++) {
+                unsigned char *rowp = rowp0 + (set * T + t) * Cfg::kATile;
+                const bool valid = t < cnt;
+#pragma unroll
+                for (int i = 0; i < NW; i++) {
+                    if (w0 + i < W) {
+                        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+                        if (valid) sign_word(Sx[i], 0x38383838u, lo, hi);
+                        *reinterpret_cast<uint4 *>(rowp + i * 256) = lo;
+                        *reinterpret_cast<uint4 *>(rowp + i * 256 + 128) = hi;
+                    }
+                }
+                // colex successor of the upper elements o[0..v) within (s, k): the lowest
+                // element that can move up moves; those below it restart at s + 1, s + 2, ...
+                const bool stepv = t + 1 < cnt;
+                const int o0 = o[0];
+                const int o1 = v >= 2 ? o[1] : k;
+                if (!__any_sync(kFull, stepv && o0 + 1 == o1)) {
+                    if (stepv) {
+                        xor_words<NW>(Sx, dT, k, o0, w0, W);
+                        o[0] = o0 + 1;
+                    }
+                } else if (stepv) {
+                    // o[0..m] = o0, o0 + 1, ..., o0 + m and o[m] can move up
+                    unsigned stop = 1u << (v - 1);
+#pragma unroll
+                    for (int i = 0; i < kMaxV - 1; i++)
+                        if (i < v - 1 && o[i] + 1 != o[i + 1]) stop |= 1u << i;
+                    const int m = __ffs(stop) - 1;
+                    const int sp = it.s + 1;
+                    xor_words<NW>(Sx, pX, k + 1, o0, w0, W);
+                    xor_words<NW>(Sx, pX, k + 1, o0 + m + 1, w0, W);
+                    xor_words<NW>(Sx, pX, k + 1, sp, w0, W);
+                    xor_words<NW>(Sx, pX, k + 1, sp + m, w0, W);
+                    xor_words<NW>(Sx, rT, k, o0 + m + 1, w0, W);
+#pragma unroll
+                    for (int i = 0; i < kMaxV; i++) o[i] = i < m ? sp + i : (i == m ? o[i] + 1 : o[i]);
+                }
+            }
+            fence_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(saddr(&sh.afull[set]));
+            j++;
+        }
+    } else {
+        // ------------------------------------------------------------- epilogue ----
+        const int quarter = warp & 3, half = warp >> 2;
+        const int r = quarter * 32 + lane;                 // tensor-memory lane = tile row
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+        long long n = 0;
+        unsigned u = 0;
+        bool ok = true;
+        int ubest = 0x7fffffff;
+        while (ok) {
+            const int slot = (int)(n % kRing);
+            if (!warp_wait(saddr(&sh.ifull[slot]), (unsigned)(n / kRing) & 1, abort_flag)) break;
+            const TcItem it = sh.ring[slot];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(saddr(&sh.ifree[slot]));
+            n++;
+            if (it.end) break;
+            for (int sl = 0; sl < it.nsl && ok; sl++) {
+                const int p0 = (it.sl0 + sl) * kTcN;
+                const int nvh = max(0, min(128, slice_heads(it, it.sl0 + sl) - 128 * half));   // columns here
+                const int nchunk = (nvh + 31) >> 5;
+                for (int t = 0; t < it.na; t++) {
+                    const int acc = (int)(u & 1);
+                    if (!warp_wait(saddr(&sh.mdone[acc]), (u >> 1) & 1, abort_flag)) { ok = false; break; }
+                    tc_after();
+                    const uint32_t col0 = lane_base + (uint32_t)(acc * kTcN);
+                    float mx = -1e30f;
+                    for (int c = 0; c < nchunk; c += 2) {
+                        const bool two = c + 1 < nchunk;
+                        if (32 * (c + 2) <= nvh || (!two && 32 * (c + 1) <= nvh)) {
+                            // whole chunks: the load returns each row's maximum
+                            float va[32], vb[32], ra = -1e30f, rb = -1e30f;
+                            tmem_ldmax32(col0 + 32u * c, va, ra);
+                            if (two) tmem_ldmax32(col0 + 32u * (c + 1), vb, rb);
+                            tmem_wait_red2(va, ra, vb, rb);
+                            mx = fmax3(mx, ra, rb);
+                        } else {
+                            // a chunk holding columns past the slice's heads: mask them
+                            uint32_t va[32], vb[32];
+#pragma unroll
+                            for (int i = 0; i < 32; i++) vb[i] = 0xff800000u;    // -inf where no second chunk
+                            tmem_ld32(col0 + 32u * c, va);
+                            if (two) tmem_ld32(col0 + 32u * (c + 1), vb);
+                            tmem_wait2(va, vb);
+                            mx = fmax3(mx, chunk_max(va, nvh - 32 * c), chunk_max(vb, two ? nvh - 32 * (c + 1) : 32));
+                        }
+                    }
+                    const int row = r * it.na + t;                 // tail index within the item
+                    const int thr = min(it.u, ubest) - a.base;
+                    const bool pass = row < it.nt && thr >= 0 && mx >= (float)(32 * W - 2 * thr);
+                    if (__any_sync(kFull, pass)) {
+                        // first column holding the row maximum = the tail's smallest rank of it
+                        int firstc = 0x7fffffff;
+                        for (int c = 0; c < nchunk; c++) {
+                            uint32_t vv[32];
+                            tmem_ld32(col0 + 32u * c, vv);
+                            tmem_wait(vv);
+#pragma unroll
+                            for (int i = 0; i < 32; i++) {
+                                const int col = 32 * c + i;
+                                if (pass && col < nvh && col < firstc && __uint_as_float(vv[i]) == mx) firstc = col;
+                            }
+                        }
+                        if (pass) {
+                            const int w = a.base + (32 * W - (int)mx) / 2;
+                            const unsigned long long rank = (unsigned long long)(p0 + 128 * half + firstc) +
+                                                            tail_rank_at(a, it.s, it.t0 + (unsigned long long)row);
+                            atomicMin(&st->key[a.level], ((unsigned long long)w << kRankBits) | rank);
+                            atomicMin(&st->U, (unsigned int)w);
+                            ubest = min(ubest, w);
+                        }
+                    }
+                    tc_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(saddr(&sh.tfree[acc]));
+                    u++;
+                }
+            }
+        }
+    }
+
+    if (sh.abort && threadIdx.x == 0) atomicExch(&st->error, MD_ETIMEOUT);
+    tc_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+// Head table of one matrix, one thread per (head, packed word): row p < C(k, q) = e4m3 signs
+// of the sum of the rows of the p-th q-subset in colex order (rows up to the next multiple of
+// 256 are zero); slice p / 256 starts at byte (p / 256) * 256 * 32 W, in the core-matrix
+// layout of the tail tiles.
+__global__ void tc_heads_kernel(const uint32_t *rows, const unsigned long long *binom, int k, int q, int W, int WP,
+                                unsigned long long nheads, unsigned long long nrows, unsigned char *heads) {
+    for (unsigned long long idx = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; idx < nrows * W;
+         idx += (unsigned long long)gridDim.x * blockDim.x) {
+        const unsigned long long p = idx / W;
+        const int w = (int)(idx % W);
+        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+        if (p < nheads) {
+            uint32_t x = 0;
+            unsigned long long t = p;
+            int top = k - 1;
+            for (int i = q; i >= 1; i--) {
+                int l = i - 1, h = top;
+                while (l < h) {
+                    const int mid = (l + h + 1) >> 1;
+                    if (binom[(size_t)mid * (k + 1) + i] <= t) l = mid; else h = mid - 1;
+                }
+                x ^= rows[l * WP + w];
+                t -= binom[(size_t)l * (k + 1) + i];
+                top = l - 1;
+            }
+            sign_word(x, 0x38383838u, lo, hi);
+        }
+        const unsigned long long slice = p / kTcN;
+        const int rr = (int)(p % kTcN);
+        unsigned char *row = heads + slice * (unsigned long long)(kTcN * 32 * W) + (rr >> 3) * (256 * W) + (rr & 7) * 16;
+        *reinterpret_cast<uint4 *>(row + (2 * w) * 128) = lo;
+        *reinterpret_cast<uint4 *>(row + (2 * w + 1) * 128) = hi;
+    }
+}
+
+template <int W>
+cudaError_t launch_tc_w(const TcArgs &a, int blocks, size_t smem, cudaStream_t s) {
+    auto kern = tc_kernel<W>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, kTcThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+size_t head_bytes(int k, int q, int W) {
+    const uint64_t nheads = binom(k, q);
+    const uint64_t slices = (nheads + kTcN - 1) / kTcN;
+    return (size_t)slices * kTcN * 32 * W;
+}
+
+}  // namespace
+
+size_t tc_tables_bytes(int k, int q, int W) { return head_bytes(k, q, W); }
+
+int tc_auto_head(int k, int W) {
+    // three-element heads keep the head dimension of the product wide for every s that
+    // carries much work; fall back to pairs when their table would be too large
+    return (k >= 4 && head_bytes(k, 3, W) <= (size_t(1) << 30)) ? 3 : 2;
+}
+
+int tc_max_upper() { return kMaxV; }
+
+int tc_smem_bytes(int k, int W, int WP) {
+    (void)WP;
+    const int bytes = 1024 + kHdrBytes + align_up((3 * k + 1) * W * 4, 1024) + 2 * tc_tiles_per_set(W) * kTcM * 32 * W +
+                      2 * kTcN * 32 * W;
+    // at least 116 KB, so that one block (holding all 512 tensor-memory columns) runs per SM
+    return bytes < 116 * 1024 ? 116 * 1024 : bytes;
+}
+
+uint64_t tc_level_items(int k, int g, int q, int W) {
+    const int v = g - q - 1;
+    if (v < 0) return 0;
+    uint64_t total = 0;
+    const uint64_t per = (uint64_t)kTcM * tc_tiles_per_set(W);
+    for (int s = q; s <= k - 1 - v; s++) {
+        const uint64_t nb = binom(s, q), nt = binom(k - 1 - s, v);
+        const uint64_t nsl = (nb + kTcN - 1) / kTcN;
+        total += ((nsl + kGroup - 1) / kGroup) * ((nt + per - 1) / per);
+    }
+    return total;
+}
+
+int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, int k, int q, int W, int WP,
+                     unsigned char *tables, void *stream) {
+    const uint64_t nheads = binom(k, q);
+    const uint64_t nrows = (nheads + kTcN - 1) / kTcN * kTcN;
+    if (nrows == 0) return 0;
+    const uint64_t total = nrows * (uint64_t)W;
+    const int blocks = (int)std::min<uint64_t>((total + 255) / 256, 8192);
+    tc_heads_kernel<<<blocks, 256, 0, (cudaStream_t)stream>>>(rows, binom_d, k, q, W, WP, nheads, nrows, tables);
+    return (int)cudaGetLastError();
+}
+
+int launch_tc_level(const unsigned char *tables, const uint32_t *rows, const unsigned long long *binom_d, DevState *st,
+                    int k, int g, int q, int base, int level, int W, int WP, int check_stop, int blocks, void *stream) {
+    TcArgs a{tables, rows, binom_d, st, k, g, q, base, level, WP, tc_tiles_per_set(W), check_stop};
+    const size_t smem = (size_t)tc_smem_bytes(k, W, WP);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    switch (W) {
+        case 1: e = launch_tc_w<1>(a, blocks, smem, s); break;
+        case 2: e = launch_tc_w<2>(a, blocks, smem, s); break;
+        case 3: e = launch_tc_w<3>(a, blocks, smem, s); break;
+        case 4: e = launch_tc_w<4>(a, blocks, smem, s); break;
+        case 5: e = launch_tc_w<5>(a, blocks, smem, s); break;
+        case 6: e = launch_tc_w<6>(a, blocks, smem, s); break;
+        case 7: e = launch_tc_w<7>(a, blocks, smem, s); break;
+        case 8: e = launch_tc_w<8>(a, blocks, smem, s); break;
+        default: return (int)cudaErrorInvalidValue;
+    }
+    return (int)e;
+}
+
+}  // namespace mdl
