@@ -34,9 +34,11 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 POPC_PER_SM_PER_CLK = 16          # measured on GB300 (popc.b32 throughput per SM per clock)
 NOMINAL_SMS = 152
 NOMINAL_MAX_MHZ = 2070.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one split_kernel launch (level g=8 of
-# rand200x100) measured with ncu on the current kernel; to be re-measured when it changes
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch (level g=8 of rand200x100) measured
+# with ncu on the current kernels; to be re-measured when a kernel changes
 SPLIT_KERNEL_TRAFFIC_BYTES = 160256 + 700928
+TC_KERNEL_TRAFFIC_BYTES = 17793280 + 0
+FP8_PER_BF16 = 2.0                # nominal dense fp8 / bf16 tensor rate (4.5 / 2.25 PFLOP/s)
 
 
 def parse():
@@ -48,6 +50,8 @@ def parse():
     ap.add_argument("--workload", default="rand200x100")
     ap.add_argument("--max-stage", type=int, default=10)
     ap.add_argument("--filter", type=int, default=1)
+    ap.add_argument("--tensor", type=int, default=1,
+                    help="1 = large levels on the tensor-core kernel (default), 0 = popcount kernels only")
     ap.add_argument("--no-time-to-d", action="store_true",
                     help="skip the full computation to d (run once on rank 0 at N=1 by default)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -151,6 +155,38 @@ def reduce_over_ranks(seconds: float, codewords: int, device: str):
     return float(t.item()), int(c.item())
 
 
+def roofline_line(args, n, k, top_g, nlaunch, per_launch_cw, per_launch_s):
+    """Roofline of the kernel that runs the deepest stage's levels."""
+    W = (n - k + 31) // 32                    # packed words of a full-rank matrix's rows
+    if args.tensor:
+        peaks = measured_peaks()
+        bf16 = peaks.get("bf16_tflops_sustained")
+        basis = "measured bf16_tflops_sustained x %.0f (nominal fp8/bf16 dense ratio)" % FP8_PER_BF16
+        if not bf16:
+            bf16, basis = 1700.0, "fallback sustained bf16 1.7 PFLOP/s x 2 (nominal fp8/bf16 dense ratio)"
+        flops_cw = 2.0 * 32 * W
+        achieved = per_launch_cw * flops_cw / per_launch_s / 1e12
+        peak = bf16 * FP8_PER_BF16
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TC_KERNEL_TRAFFIC_BYTES,
+                "traffic_note": "dram read+write per launch, ncu on the same kernel (level g=8 launch): the "
+                                "head-table stream, fixed per launch, does not grow with codewords",
+                "kernel": "tc_kernel<%d> (stage g=%d levels, %d launches timed)" % (W, top_g, nlaunch),
+                "peak_basis": basis,
+                "work_basis": "%d flops per codeword: a +-1 e4m3 inner product over the %d packed bits "
+                              "(tcgen05.mma kind::f8f6f4, K = 32 per instruction)" % (flops_cw, 32 * W)}
+    peak = POPC_PER_SM_PER_CLK * NOMINAL_SMS * NOMINAL_MAX_MHZ * 1e6 / 1e9       # Gpopc/s
+    achieved = per_launch_cw * 1.0 / per_launch_s / 1e9                              # 1 popc per codeword (filtered)
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpopc/s", "frac": achieved / peak,
+            "traffic": SPLIT_KERNEL_TRAFFIC_BYTES,
+            "traffic_note": "dram read+write per launch, ncu on the same kernel (level g=8 launch); "
+                            "fixed staging cost, does not grow with codewords",
+            "kernel": "split_kernel (stage g=%d levels, %d launches timed)" % (top_g, nlaunch),
+            "peak_basis": "16 popc/clk/SM (measured) x 152 SMs x 2070 MHz max clock",
+            "work_basis": "1 popc per codeword: popcount of the OR of the packed words, exact weight "
+                          "only for codewords that can reach U"}
+
+
 def measured_peaks():
     try:
         with open(PEAKS) as f:
@@ -231,7 +267,8 @@ def run_ours(args):
 
     G, n, k = inputs.single_code(args.workload)
     stream = torch.cuda.current_stream()
-    opt = B.md_options_init(max_stage=args.max_stage, filter=args.filter, stream=stream.cuda_stream)
+    opt = B.md_options_init(max_stage=args.max_stage, filter=args.filter, tensor=args.tensor,
+                            stream=stream.cuda_stream)
     h = B.md_create(G, n, k, opt)
     l2_flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
 
@@ -280,16 +317,7 @@ def run_ours(args):
     top_s = sum(lv[5] for lv in top)
     per_launch_cw = top_cw / len(top)
     per_launch_s = top_s / len(top)
-    peak = POPC_PER_SM_PER_CLK * NOMINAL_SMS * NOMINAL_MAX_MHZ * 1e6 / 1e9       # Gpopc/s
-    achieved = per_launch_cw * 1.0 / per_launch_s / 1e9                              # 1 popc per codeword (filtered)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpopc/s", "frac": achieved / peak,
-                "traffic": SPLIT_KERNEL_TRAFFIC_BYTES,
-                "traffic_note": "dram read+write per launch, ncu on the same kernel (level g=8 launch); "
-                                "fixed staging cost, does not grow with codewords",
-                "kernel": "split_kernel (stage g=%d levels, %d launches timed)" % (top_g, len(top)),
-                "peak_basis": "16 popc/clk/SM (measured) x 152 SMs x 2070 MHz max clock",
-                "work_basis": "1 popc per codeword: popcount of the OR of the packed words, exact weight "
-                              "only for codewords that can reach U"}
+    roofline = roofline_line(args, n, k, top_g, len(top), per_launch_cw, per_launch_s)
 
     line = {
         "metric": "codewords/s", "value": value, "unit": "codewords/s", "n_gpus": ws, "steps": args.steps,
@@ -304,7 +332,7 @@ def run_ours(args):
 
     if rank == 0 and not args.no_e2e:
         # end to end through the C ABI from host buffers: create (host G), compute, destroy
-        opt_e = B.md_options_init(max_stage=args.max_stage, filter=args.filter)
+        opt_e = B.md_options_init(max_stage=args.max_stage, filter=args.filter, tensor=args.tensor)
         times, h2d, d2h, cwe = [], 0, 0, 0
         for _ in range(args.steps):
             t0 = time.perf_counter()
@@ -327,7 +355,7 @@ def run_ours(args):
                                           % (args.max_stage, size, dt)}
 
     if rank == 0 and ws == 1 and not args.no_time_to_d and args.workload == "rand200x100":
-        opt_f = B.md_options_init(filter=args.filter, stream=stream.cuda_stream)
+        opt_f = B.md_options_init(filter=args.filter, tensor=args.tensor, stream=stream.cuda_stream)
         hf = B.md_create(G, n, k, opt_f)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -468,7 +496,7 @@ def run_profile_once(args):
     from paper_1911_08963_gb300 import binding as B
     from paper_1911_08963_gb300 import inputs
     G, n, k = inputs.single_code(args.workload)
-    h = B.md_create(G, n, k, B.md_options_init(max_stage=args.max_stage, filter=args.filter))
+    h = B.md_create(G, n, k, B.md_options_init(max_stage=args.max_stage, filter=args.filter, tensor=args.tensor))
     d, _ = B.md_compute(h, n)
     info = B.md_info_get(h)
     B.md_destroy(h)
