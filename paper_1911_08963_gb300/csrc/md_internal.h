@@ -111,7 +111,7 @@ struct PlanOptions {
 
 // ---- tensor-core levels (md_tc.cu) ----
 size_t tc_tables_bytes(int k, int q, int W);  // head table of one matrix
-int tc_smem_bytes(int k, int W, int WP);
+int tc_smem_bytes(int k, int W, int optin, int *with_bsub);
 uint64_t tc_level_items(int k, int g, int q, int W);
 int tc_auto_head(int k, int W);     // q used when PlanOptions::tensor_head is 0
 int tc_max_upper();                 // largest g - q - 1 the tensor-core kernel handles

@@ -17,10 +17,9 @@
 //     256-row slices of 8-row x 16-byte core matrices (the K-major operand layout without
 //     swizzle), built once per matrix and copied slice by slice into shared memory with bulk
 //     copies (cp.async.bulk, completion on an mbarrier).
-//   * Tails: eight producer warps, two threads per tile row (each owns half of the packed
-//     words); a thread walks its own run of consecutive tails in colex order, keeping its
-//     words of the tail sum in registers, and writes the e4m3 signs of those words: two
-//     16-byte stores per packed word.  A colex step moves a run of consecutive elements
+//   * Tails: two producer warps, two tile rows per thread; for each of its rows a thread
+//     walks its own run of consecutive tails in colex order, keeping the tail sum in
+//     registers, and writes its e4m3 signs: two 16-byte stores per packed word.  A colex step moves a run of consecutive elements
 //     o0..o0+m: they leave, s+1..s+m and o0+m+1 enter, which prefix XORs of the rows give in
 //     five lookups whatever m is (usually m = 0: one XOR with the difference of two adjacent
 //     rows).  The rows, their adjacent differences and prefix XORs sit in shared memory
@@ -34,7 +33,8 @@
 //     256), two accumulators of 256 columns so the next product overlaps the epilogue.
 //   * Eight epilogue warps (two per tensor-memory lane quarter, one per half of the columns)
 //     read D with tcgen05.ld.red, which also returns each lane's maximum over the columns
-//     it loads, so no per-element arithmetic is left; a row reaching
+//     it loads, so no per-element arithmetic is left; the four loads of a half are in flight
+//     together (one round trip per accumulator); a row reaching
 //     K - 2 (min(U, best) - base) is resolved to (weight, first rank) and published with
 //     atomicMin, as in the other level kernels.
 //   * One scheduler thread takes work items (s, head slices, run of tails) from the level's
@@ -58,12 +58,14 @@ using namespace dev;
 
 constexpr int kTcM = 128;                  // tails per tile (tensor-memory lanes)
 constexpr int kTcN = 256;                  // heads per slice (accumulator columns)
+// 12 warps = 3 per SM sub-partition, so every thread can have 168 registers: an epilogue warp
+// then keeps a whole 128-column half of an accumulator (four loads) in flight at once.
 constexpr int kEpiWarps = 8;               // warps 0-7
-constexpr int kProdWarp0 = 8;              // warps 8-15
-constexpr int kProdWarps = 8;
-constexpr int kMmaWarp = 16;
-constexpr int kSchedWarp = 17;
-constexpr int kTcWarps = 18;
+constexpr int kProdWarp0 = 8;              // warps 8-9: two tile rows per thread
+constexpr int kProdWarps = 2;
+constexpr int kMmaWarp = 10;
+constexpr int kSchedWarp = 11;
+constexpr int kTcWarps = 12;
 constexpr int kTcThreads = kTcWarps * 32;
 constexpr int kRing = 8;                   // work items between the scheduler and the others
 constexpr int kItemReaders = kEpiWarps + kProdWarps + 1;   // warps that take each ring entry
@@ -100,14 +102,14 @@ struct TcItem {
 __device__ __forceinline__ int slice_heads(const TcItem &it, int sl) { return min(kTcN, it.nb - sl * kTcN); }
 
 struct TcShared {
-    unsigned long long afull[2];           // producers -> MMA: tail set written (8 warp arrivals)
+    unsigned long long afull[2];           // producers -> MMA: tail set written (2 warp arrivals)
     unsigned long long afree[2];           // MMA -> producers: products reading the set done
     unsigned long long mdone[2];           // MMA -> epilogue: accumulator complete
     unsigned long long tfree[2];           // epilogue -> MMA: accumulator read (8 arrivals)
     unsigned long long bfull[2];           // head slice landed (transaction count)
     unsigned long long bfree[2];           // MMA -> MMA: products reading the slice complete
     unsigned long long ifull[kRing];       // scheduler -> readers
-    unsigned long long ifree[kRing];       // readers -> scheduler (17 warp arrivals)
+    unsigned long long ifree[kRing];       // readers -> scheduler (11 warp arrivals)
     TcItem ring[kRing];
     unsigned long long cum[kMaxN + 1];     // work items before s
     uint32_t taddr;
@@ -145,6 +147,19 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Non-blocking: has the phase of parity `parity` completed?
+__device__ __forceinline__ bool mbar_poll(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
         : "=r"(ok)
         : "r"(bar), "r"(parity)
@@ -312,6 +327,7 @@ struct TcArgs {
     const unsigned long long *binom;       // (k + 1) x (k + 1)
     DevState *st;
     int k, g, q, base, level, WP, tiles, check_stop;   // tiles: tail tiles per set
+    int bsub;                              // 1: C(x, i), i <= kMaxV, staged in shared memory
 };
 
 __device__ __forceinline__ unsigned long long C(const TcArgs &a, int n, int r) {
@@ -328,15 +344,22 @@ __device__ __forceinline__ int colex_digit(const TcArgs &a, int lo, int hi, int 
 }
 
 // Tail index t (colex among the v-subsets of [s + 1, k)) -> its elements o[0..v), in registers.
-__device__ __forceinline__ void tail_unrank(const TcArgs &a, int s, int v, unsigned long long t, int (&o)[kMaxV]) {
+// bs: C(x, i) at bs[x * (kMaxV + 1) + i] in shared memory, or null for the global table.
+__device__ __forceinline__ void tail_unrank(const TcArgs &a, const unsigned long long *bs, int s, int v,
+                                            unsigned long long t, int (&o)[kMaxV]) {
     int top = a.k - 2 - s;
 #pragma unroll
     for (int i = kMaxV; i >= 1; i--) {
         if (i <= v) {
-            const int x = colex_digit(a, i - 1, top, i, t);
-            o[i - 1] = x + s + 1;
-            t -= C(a, x, i);
-            top = x - 1;
+            int lo = i - 1, hi = top;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                const unsigned long long c = bs ? bs[mid * (kMaxV + 1) + i] : C(a, mid, i);
+                if (c <= t) lo = mid; else hi = mid - 1;
+            }
+            o[i - 1] = lo + s + 1;
+            t -= bs ? bs[lo * (kMaxV + 1) + i] : C(a, lo, i);
+            top = lo - 1;
         }
     }
 }
@@ -388,6 +411,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
     uint32_t *pX = dT + W * a.k;
     unsigned char *Atile = smem + kHdrBytes + align_up((3 * a.k + 1) * W * 4, 1024);   // [2][T] tiles
     unsigned char *Btile = Atile + 2 * T * Cfg::kATile;                                // [2] slices
+    unsigned long long *bsub = a.bsub ? reinterpret_cast<unsigned long long *>(Btile + 2 * Cfg::kBTile) : nullptr;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     DevState *st = a.st;
@@ -425,6 +449,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
         }
     }
     for (int s = threadIdx.x; s < k; s += blockDim.x) sh.cum[s + 1] = items_of(a, s);
+    if (bsub)
+        for (int i = threadIdx.x; i < (k + 1) * (kMaxV + 1); i += blockDim.x)
+            bsub[i] = C(a, i / (kMaxV + 1), i % (kMaxV + 1));
     __syncthreads();
     if (threadIdx.x == 0) {
         sh.cum[0] = 0;
@@ -537,6 +564,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                     if (pend_buf == bb) pend_buf = -1;
                     const uint32_t idesc = idesc_e4m3((slice_heads(cur, cur.sl0 + sl) + 15) & ~15);
                     const uint32_t bbase = saddr(Btile + bb * Cfg::kBTile);
+                    // the next slice (of this item or the next) goes into the other buffer as
+                    // soon as the products of the slice before this one are done with it
+                    const TcItem *ni = &cur;
+                    int nsl_idx = cur.sl0 + sl + 1;
+                    if (sl + 1 == cur.nsl) {
+                        if (!take(nxt)) { ok = false; break; }
+                        ni = &nxt;
+                        nsl_idx = nxt.sl0;
+                    }
+                    bool fetched = ni->end != 0;
+                    const uint32_t prev_free = saddr(&sh.bfree[(step + 1) & 1]);
+                    const unsigned prev_parity = (unsigned)((step - 1) >> 1) & 1;
                     for (int t = 0; t < cur.na; t++) {
                         const int acc = (int)(u & 1);
                         if (u >= 2 && !mbar_wait(saddr(&sh.tfree[acc]), ((u >> 1) - 1) & 1, abort_flag)) {
@@ -554,21 +593,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                         last_acc = acc;
                         last_parity = (u >> 1) & 1;
                         u++;
+                        if (!fetched && (step == 0 || mbar_poll(prev_free, prev_parity))) {
+                            load_slice(*ni, nsl_idx, step + 1);
+                            fetched = true;
+                        }
                     }
                     if (!ok) break;
                     mma_commit(saddr(&sh.bfree[bb]));
-                    // the next slice (of this item or the next) goes into the other buffer once
-                    // the products of the slice before this one are done with it
-                    const TcItem *ni = &cur;
-                    int nsl_idx = cur.sl0 + sl + 1;
-                    if (sl + 1 == cur.nsl) {
-                        if (!take(nxt)) { ok = false; break; }
-                        ni = &nxt;
-                        nsl_idx = nxt.sl0;
-                    }
-                    if (!ni->end) {
-                        if (step >= 1 &&
-                            !mbar_wait(saddr(&sh.bfree[(step + 1) & 1]), (unsigned)((step - 1) >> 1) & 1, abort_flag)) {
+                    if (!fetched) {
+                        if (step >= 1 && !mbar_wait(prev_free, prev_parity, abort_flag)) {
                             ok = false;
                             break;
                         }
@@ -587,18 +620,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
         }
     } else if (warp >= kProdWarp0) {
         // ------------------------------------------------------------ producers ----
-        // two threads per tile row: part h owns packed words [h * NW, h * NW + NW)
-        constexpr int NW = (W + 1) / 2;
-        const int pw = warp - kProdWarp0;
-        const int part = pw >> 2;
-        const int r = (pw & 3) * 32 + lane;                // tile row
-        const int w0 = part * NW;
+        constexpr int NW = W;
+        const int w0 = 0;
         long long n = 0, j = 0;
         int o[kMaxV];                                      // upper elements of the current tail
 #pragma unroll
         for (int i = 0; i < kMaxV; i++) o[i] = 0;
-        uint32_t Sx[NW];                                   // this thread's words of the tail sum
-        unsigned char *rowp0 = Atile + (r >> 3) * Cfg::kSbo + (r & 7) * 16 + w0 * 256;
+        uint32_t Sx[NW];                                   // the tail sum
         for (;;) {
             const int slot = (int)(n % kRing);
             if (!warp_wait(saddr(&sh.ifull[slot]), (unsigned)(n / kRing) & 1, abort_flag)) break;
@@ -609,54 +637,56 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             if (it.end) break;
             const int set = (int)(j & 1);
             if (j >= 2 && !warp_wait(saddr(&sh.afree[set]), (unsigned)((j >> 1) - 1) & 1, abort_flag)) break;
-            const int first = r * it.na;
-            const int cnt = max(0, min(it.na, it.nt - first));
+            for (int half = 0; half < 2; half++) {
+                const int r = (warp - kProdWarp0) * 32 + lane + 64 * half;   // tile row
+                unsigned char *rowp0 = Atile + (r >> 3) * Cfg::kSbo + (r & 7) * 16;
+                const int first = r * it.na;
+                const int cnt = max(0, min(it.na, it.nt - first));
 #pragma unroll
-            for (int i = 0; i < NW; i++) Sx[i] = 0;
-            if (cnt > 0) {
-                tail_unrank(a, it.s, v, it.t0 + (unsigned long long)first, o);
-                xor_words<NW>(Sx, rT, k, it.s, w0, W);
+                for (int i = 0; i < NW; i++) Sx[i] = 0;
+                if (cnt > 0) {
+                    tail_unrank(a, bsub, it.s, v, it.t0 + (unsigned long long)first, o);
+                    xor_words<NW>(Sx, rT, k, it.s, w0, W);
 #pragma unroll
-                for (int i = 0; i < kMaxV; i++)
-                    if (i < v) xor_words<NW>(Sx, rT, k, o[i], w0, W);
-            }
-            for (int t = 0; t < it.na; t++) {
-                unsigned char *rowp = rowp0 + (set * T + t) * Cfg::kATile;
-                const bool valid = t < cnt;
+                    for (int i = 0; i < kMaxV; i++)
+                        if (i < v) xor_words<NW>(Sx, rT, k, o[i], w0, W);
+                }
+                for (int t = 0; t < it.na; t++) {
+                    unsigned char *rowp = rowp0 + (set * T + t) * Cfg::kATile;
+                    const bool valid = t < cnt;
 #pragma unroll
-                for (int i = 0; i < NW; i++) {
-                    if (w0 + i < W) {
+                    for (int i = 0; i < NW; i++) {
                         uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
                         if (valid) sign_word(Sx[i], 0x38383838u, lo, hi);
                         *reinterpret_cast<uint4 *>(rowp + i * 256) = lo;
                         *reinterpret_cast<uint4 *>(rowp + i * 256 + 128) = hi;
                     }
-                }
-                // colex successor of the upper elements o[0..v) within (s, k): the lowest
-                // element that can move up moves; those below it restart at s + 1, s + 2, ...
-                const bool stepv = t + 1 < cnt;
-                const int o0 = o[0];
-                const int o1 = v >= 2 ? o[1] : k;
-                if (!__any_sync(kFull, stepv && o0 + 1 == o1)) {
-                    if (stepv) {
-                        xor_words<NW>(Sx, dT, k, o0, w0, W);
-                        o[0] = o0 + 1;
+                    // colex successor of the upper elements o[0..v) within (s, k): the lowest
+                    // element that can move up moves; those below it restart at s + 1, s + 2, ...
+                    const bool stepv = t + 1 < cnt;
+                    const int o0 = o[0];
+                    const int o1 = v >= 2 ? o[1] : k;
+                    if (!__any_sync(kFull, stepv && o0 + 1 == o1)) {
+                        if (stepv) {
+                            xor_words<NW>(Sx, dT, k, o0, w0, W);
+                            o[0] = o0 + 1;
+                        }
+                    } else if (stepv) {
+                        // o[0..m] = o0, o0 + 1, ..., o0 + m and o[m] can move up
+                        unsigned stop = 1u << (v - 1);
+#pragma unroll
+                        for (int i = 0; i < kMaxV - 1; i++)
+                            if (i < v - 1 && o[i] + 1 != o[i + 1]) stop |= 1u << i;
+                        const int m = __ffs(stop) - 1;
+                        const int sp = it.s + 1;
+                        xor_words<NW>(Sx, pX, k + 1, o0, w0, W);
+                        xor_words<NW>(Sx, pX, k + 1, o0 + m + 1, w0, W);
+                        xor_words<NW>(Sx, pX, k + 1, sp, w0, W);
+                        xor_words<NW>(Sx, pX, k + 1, sp + m, w0, W);
+                        xor_words<NW>(Sx, rT, k, o0 + m + 1, w0, W);
+#pragma unroll
+                        for (int i = 0; i < kMaxV; i++) o[i] = i < m ? sp + i : (i == m ? o[i] + 1 : o[i]);
                     }
-                } else if (stepv) {
-                    // o[0..m] = o0, o0 + 1, ..., o0 + m and o[m] can move up
-                    unsigned stop = 1u << (v - 1);
-#pragma unroll
-                    for (int i = 0; i < kMaxV - 1; i++)
-                        if (i < v - 1 && o[i] + 1 != o[i + 1]) stop |= 1u << i;
-                    const int m = __ffs(stop) - 1;
-                    const int sp = it.s + 1;
-                    xor_words<NW>(Sx, pX, k + 1, o0, w0, W);
-                    xor_words<NW>(Sx, pX, k + 1, o0 + m + 1, w0, W);
-                    xor_words<NW>(Sx, pX, k + 1, sp, w0, W);
-                    xor_words<NW>(Sx, pX, k + 1, sp + m, w0, W);
-                    xor_words<NW>(Sx, rT, k, o0 + m + 1, w0, W);
-#pragma unroll
-                    for (int i = 0; i < kMaxV; i++) o[i] = i < m ? sp + i : (i == m ? o[i] + 1 : o[i]);
                 }
             }
             fence_async_smem();
@@ -691,6 +721,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                     tc_after();
                     const uint32_t col0 = lane_base + (uint32_t)(acc * kTcN);
                     float mx = -1e30f;
+                    if (nvh == 128) {
+                        // all four chunks whole: one round trip
+                        float v0[32], v1[32], v2[32], v3[32], r0, r1, r2, r3;
+                        tmem_ldmax32(col0, v0, r0);
+                        tmem_ldmax32(col0 + 32u, v1, r1);
+                        tmem_ldmax32(col0 + 64u, v2, r2);
+                        tmem_ldmax32(col0 + 96u, v3, r3);
+                        tmem_wait_red2(v0, r0, v1, r1);
+                        tmem_wait_red2(v2, r2, v3, r3);
+                        mx = fmax3(fmax3(r0, r1, r2), r3, mx);
+                    } else
                     for (int c = 0; c < nchunk; c += 2) {
                         const bool two = c + 1 < nchunk;
                         if (32 * (c + 2) <= nvh || (!two && 32 * (c + 1) <= nvh)) {
@@ -817,11 +858,19 @@ int tc_auto_head(int k, int W) {
 
 int tc_max_upper() { return kMaxV; }
 
-int tc_smem_bytes(int k, int W, int WP) {
-    (void)WP;
-    const int bytes = 1024 + kHdrBytes + align_up((3 * k + 1) * W * 4, 1024) + 2 * tc_tiles_per_set(W) * kTcM * 32 * W +
-                      2 * kTcN * 32 * W;
-    // at least 116 KB, so that one block (holding all 512 tensor-memory columns) runs per SM
+// Shared memory without / with the binomial sub-table of the producers.
+int tc_smem_base(int k, int W) {
+    return 1024 + kHdrBytes + align_up((3 * k + 1) * W * 4, 1024) + 2 * tc_tiles_per_set(W) * kTcM * 32 * W +
+           2 * kTcN * 32 * W;
+}
+int tc_bsub_bytes(int k) { return (k + 1) * (kMaxV + 1) * 8; }
+
+// Dynamic shared memory of a launch, with the binomial sub-table when it fits in `optin`;
+// at least 116 KB, so that one block (holding all 512 tensor-memory columns) runs per SM.
+int tc_smem_bytes(int k, int W, int optin, int *with_bsub) {
+    int bytes = tc_smem_base(k, W);
+    *with_bsub = bytes + tc_bsub_bytes(k) <= optin ? 1 : 0;
+    if (*with_bsub) bytes += tc_bsub_bytes(k);
     return bytes < 116 * 1024 ? 116 * 1024 : bytes;
 }
 
@@ -851,8 +900,12 @@ int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, in
 
 int launch_tc_level(const unsigned char *tables, const uint32_t *rows, const unsigned long long *binom_d, DevState *st,
                     int k, int g, int q, int base, int level, int W, int WP, int check_stop, int blocks, void *stream) {
-    TcArgs a{tables, rows, binom_d, st, k, g, q, base, level, WP, tc_tiles_per_set(W), check_stop};
-    const size_t smem = (size_t)tc_smem_bytes(k, W, WP);
+    int dev = 0, optin = 0, with_bsub = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return (int)cudaErrorInvalidValue;
+    const size_t smem = (size_t)tc_smem_bytes(k, W, optin, &with_bsub);
+    TcArgs a{tables, rows, binom_d, st, k, g, q, base, level, WP, tc_tiles_per_set(W), check_stop, with_bsub};
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     switch (W) {
