@@ -17,8 +17,9 @@
 //     256-row slices of 8-row x 16-byte core matrices (the K-major operand layout without
 //     swizzle), built once per matrix and copied slice by slice into shared memory with bulk
 //     copies (cp.async.bulk, completion on an mbarrier).
-//   * Tails: two producer warps, two tile rows per thread; for each of its rows a thread
-//     walks its own run of consecutive tails in colex order, keeping the tail sum in
+//   * Tails: two producer warps, two tile rows per thread; a thread unranks one tail per
+//     item and walks its 2 na consecutive tails in colex order (the first na fill its first
+//     row across the item's tiles, the rest its second row), keeping the tail sum in
 //     registers, and writes its e4m3 signs: two 16-byte stores per packed word.  A colex step moves a run of consecutive elements
 //     o0..o0+m: they leave, s+1..s+m and o0+m+1 enter, which prefix XORs of the rows give in
 //     five lookups whatever m is (usually m = 0: one XOR with the difference of two adjacent
@@ -345,21 +346,32 @@ __device__ __forceinline__ int colex_digit(const TcArgs &a, int lo, int hi, int 
 
 // Tail index t (colex among the v-subsets of [s + 1, k)) -> its elements o[0..v), in registers.
 // bs: C(x, i) at bs[x * (kMaxV + 1) + i] in shared memory, or null for the global table.
+// Each digit (the largest x with C(x, i) <= t) starts from C(x, i) ~ (x - (i-1)/2)^i / i!,
+// i.e. x ~ (i! t)^(1/i) + (i-1)/2, and is then corrected with exact comparisons (one or two
+// steps instead of a binary search).
 __device__ __forceinline__ void tail_unrank(const TcArgs &a, const unsigned long long *bs, int s, int v,
                                             unsigned long long t, int (&o)[kMaxV]) {
     int top = a.k - 2 - s;
+    float fact = 1.f;
+    for (int i = 2; i <= v; i++) fact *= (float)i;
 #pragma unroll
     for (int i = kMaxV; i >= 1; i--) {
         if (i <= v) {
-            int lo = i - 1, hi = top;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                const unsigned long long c = bs ? bs[mid * (kMaxV + 1) + i] : C(a, mid, i);
-                if (c <= t) lo = mid; else hi = mid - 1;
+            auto Cb = [&](int x) { return bs ? bs[x * (kMaxV + 1) + i] : C(a, x, i); };
+            const int lo = i - 1, hi = top;
+            int x;
+            if (i == 1) {
+                x = (int)min((unsigned long long)hi, t);
+            } else {
+                const float est = exp2f(__log2f(fmaxf((float)t, 1.f) * fact) / (float)i) + 0.5f * (float)(i - 1);
+                x = max(lo, min(hi, (int)est));
+                while (x < hi && Cb(x + 1) <= t) x++;
+                while (x > lo && Cb(x) > t) x--;
             }
-            o[i - 1] = lo + s + 1;
-            t -= bs ? bs[lo * (kMaxV + 1) + i] : C(a, lo, i);
-            top = lo - 1;
+            o[i - 1] = x + s + 1;
+            t -= Cb(x);
+            top = x - 1;
+            fact /= (float)i;
         }
     }
 }
@@ -637,11 +649,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             if (it.end) break;
             const int set = (int)(j & 1);
             if (j >= 2 && !warp_wait(saddr(&sh.afree[set]), (unsigned)((j >> 1) - 1) & 1, abort_flag)) break;
-            for (int half = 0; half < 2; half++) {
-                const int r = (warp - kProdWarp0) * 32 + lane + 64 * half;   // tile row
-                unsigned char *rowp0 = Atile + (r >> 3) * Cfg::kSbo + (r & 7) * 16;
-                const int first = r * it.na;
-                const int cnt = max(0, min(it.na, it.nt - first));
+            {
+                // thread p walks tails [2 na p, 2 na p + 2 na): the first na go to tile row p,
+                // the next na to row p + 64 (tile t of each)
+                const int p = (warp - kProdWarp0) * 32 + lane;
+                const int first = 2 * it.na * p;
+                const int cnt = max(0, min(2 * it.na, it.nt - first));
 #pragma unroll
                 for (int i = 0; i < NW; i++) Sx[i] = 0;
                 if (cnt > 0) {
@@ -651,9 +664,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                     for (int i = 0; i < kMaxV; i++)
                         if (i < v) xor_words<NW>(Sx, rT, k, o[i], w0, W);
                 }
-                for (int t = 0; t < it.na; t++) {
-                    unsigned char *rowp = rowp0 + (set * T + t) * Cfg::kATile;
-                    const bool valid = t < cnt;
+                for (int m = 0; m < 2 * it.na; m++) {
+                    const int r = m < it.na ? p : p + 64;
+                    const int t = m < it.na ? m : m - it.na;
+                    unsigned char *rowp = Atile + (set * T + t) * Cfg::kATile + (r >> 3) * Cfg::kSbo + (r & 7) * 16;
+                    const bool valid = m < cnt;
 #pragma unroll
                     for (int i = 0; i < NW; i++) {
                         uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
@@ -663,7 +678,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                     }
                     // colex successor of the upper elements o[0..v) within (s, k): the lowest
                     // element that can move up moves; those below it restart at s + 1, s + 2, ...
-                    const bool stepv = t + 1 < cnt;
+                    const bool stepv = m + 1 < cnt;
                     const int o0 = o[0];
                     const int o1 = v >= 2 ? o[1] : k;
                     if (!__any_sync(kFull, stepv && o0 + 1 == o1)) {
@@ -677,15 +692,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
 #pragma unroll
                         for (int i = 0; i < kMaxV - 1; i++)
                             if (i < v - 1 && o[i] + 1 != o[i + 1]) stop |= 1u << i;
-                        const int m = __ffs(stop) - 1;
+                        const int mm = __ffs(stop) - 1;
                         const int sp = it.s + 1;
                         xor_words<NW>(Sx, pX, k + 1, o0, w0, W);
-                        xor_words<NW>(Sx, pX, k + 1, o0 + m + 1, w0, W);
+                        xor_words<NW>(Sx, pX, k + 1, o0 + mm + 1, w0, W);
                         xor_words<NW>(Sx, pX, k + 1, sp, w0, W);
-                        xor_words<NW>(Sx, pX, k + 1, sp + m, w0, W);
-                        xor_words<NW>(Sx, rT, k, o0 + m + 1, w0, W);
+                        xor_words<NW>(Sx, pX, k + 1, sp + mm, w0, W);
+                        xor_words<NW>(Sx, rT, k, o0 + mm + 1, w0, W);
 #pragma unroll
-                        for (int i = 0; i < kMaxV; i++) o[i] = i < m ? sp + i : (i == m ? o[i] + 1 : o[i]);
+                        for (int i = 0; i < kMaxV; i++) o[i] = i < mm ? sp + i : (i == mm ? o[i] + 1 : o[i]);
                     }
                 }
             }
@@ -752,7 +767,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                             mx = fmax3(mx, chunk_max(va, nvh - 32 * c), chunk_max(vb, two ? nvh - 32 * (c + 1) : 32));
                         }
                     }
-                    const int row = r * it.na + t;                 // tail index within the item
+                    // tail index within the item: row r of tile t is tail 2 na (r mod 64) + na (r / 64) + t
+                    const int row = 2 * it.na * (r & 63) + it.na * (r >> 6) + t;
                     const int thr = min(it.u, ubest) - a.base;
                     const bool pass = row < it.nt && thr >= 0 && mx >= (float)(32 * W - 2 * thr);
                     if (__any_sync(kFull, pass)) {
