@@ -23,7 +23,9 @@ struct DevLayout {
     char *base = nullptr;
     size_t bytes = 0;
     std::vector<uint32_t *> rows, h2;
-    std::vector<unsigned char *> heads;     // tensor-core tables per matrix (null: none)
+    std::vector<unsigned char *> heads;     // tensor-core head tables per matrix (null: none)
+    std::vector<unsigned char *> heads2;    // second-phase (q+1)-head tables
+    std::vector<int> tc_smin;
     unsigned long long *binom = nullptr;
     MEntry *mtab = nullptr;
     DevState *st = nullptr;
@@ -132,11 +134,14 @@ int setup_device(md_ctx *h) {
         }
 
     // head size of each matrix's tensor-core levels (0: it has none)
-    std::vector<int> tc_q(m, 0);
+    std::vector<int> tc_q(m, 0), tc_smin(m, 0);
     for (const LevelPlan &p : h->plans)
-        if (p.kind == KIND_TC) tc_q[p.j] = p.tc_q;
+        if (p.kind == KIND_TC) {
+            tc_q[p.j] = p.tc_q;
+            tc_smin[p.j] = std::max(tc_smin[p.j], p.tc_smin);
+        }
     size_t off = 0;
-    std::vector<size_t> rows_off(m), h2_off(m), heads_off(m, 0);
+    std::vector<size_t> rows_off(m), h2_off(m), heads_off(m, 0), heads2_off(m, 0);
     for (int j = 0; j < m; j++) {
         rows_off[j] = off;
         off = align256(off + (size_t)k * c.gam[j].WP * 4);
@@ -145,6 +150,8 @@ int setup_device(md_ctx *h) {
         if (tc_q[j]) {
             heads_off[j] = off;
             off = align256(off + tc_tables_bytes(k, tc_q[j], c.gam[j].W));
+            heads2_off[j] = off;      // (q+1)-heads of the second phase: the first C(s_min, q+1)
+            off = align256(off + tc_heads_bytes(binom(tc_smin[j], tc_q[j] + 1), c.gam[j].W) + 256);
         }
     }
     const size_t binom_off = off;
@@ -172,10 +179,15 @@ int setup_device(md_ctx *h) {
     h->dev.rows.resize(m);
     h->dev.h2.resize(m);
     h->dev.heads.assign(m, nullptr);
+    h->dev.heads2.assign(m, nullptr);
+    h->dev.tc_smin = tc_smin;
     for (int j = 0; j < m; j++) {
         h->dev.rows[j] = (uint32_t *)(h->dev.base + rows_off[j]);
         h->dev.h2[j] = (uint32_t *)(h->dev.base + h2_off[j]);
-        if (tc_q[j]) h->dev.heads[j] = (unsigned char *)(h->dev.base + heads_off[j]);
+        if (tc_q[j]) {
+            h->dev.heads[j] = (unsigned char *)(h->dev.base + heads_off[j]);
+            h->dev.heads2[j] = (unsigned char *)(h->dev.base + heads2_off[j]);
+        }
     }
     h->dev.binom = (unsigned long long *)(h->dev.base + binom_off);
     h->dev.mtab = (MEntry *)(h->dev.base + mtab_off);
@@ -201,8 +213,11 @@ int setup_device(md_ctx *h) {
     for (int j = 0; ok && j < m; j++)
         if (tc_q[j]) {
             ok = launch_tc_tables(h->dev.rows[j], h->dev.binom, k, tc_q[j], c.gam[j].W, c.gam[j].WP,
-                                  h->dev.heads[j], s) == 0;
-            head_tables++;
+                                  binom(k, tc_q[j]), h->dev.heads[j], s) == 0;
+            const uint64_t n2 = binom(tc_smin[j], tc_q[j] + 1);
+            if (ok && n2) ok = launch_tc_tables(h->dev.rows[j], h->dev.binom, k, tc_q[j] + 1, c.gam[j].W,
+                                                c.gam[j].WP, n2, h->dev.heads2[j], s) == 0;
+            head_tables += 2;
         }
     if (ok) ok = cudaStreamSynchronize(s) == cudaSuccess;
     if (!ok) { cudaGetLastError(); free_device(h); return MD_ECUDA; }
@@ -392,8 +407,9 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
             LevelArgs a;
             if (p.kind == KIND_TC) {
                 a = level_args(h, p, level, false);
-                err |= launch_tc_level(h->dev.heads[p.j], h->dev.rows[p.j], h->dev.binom, h->dev.st, k, p.g, p.tc_q,
-                                       p.base, level, c.gam[p.j].W, c.gam[p.j].WP, 1, h->sms, s) != 0;
+                err |= launch_tc_level(h->dev.heads[p.j], h->dev.heads2[p.j], p.tc_smin, h->dev.rows[p.j],
+                                       h->dev.binom, h->dev.st, k, p.g, p.tc_q, p.base, level, c.gam[p.j].W,
+                                       c.gam[p.j].WP, 1, h->sms, s) != 0;
             } else {
                 LaunchCfg L = launch_cfg(h, p);
                 a = level_args(h, p, level, L.h2s);

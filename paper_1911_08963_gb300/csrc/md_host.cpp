@@ -371,7 +371,8 @@ LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o) {
             p.kind = KIND_TC;
             p.tc_q = q;
             p.v = v;
-            p.nchunks = tc_level_items(k, g, q, gm.W);
+            p.tc_smin = g >= q + 2 ? tc_split_point(k, q) : q;
+            p.nchunks = tc_level_items(k, g, q, p.tc_smin, gm.W);
             return p;
         }
     }

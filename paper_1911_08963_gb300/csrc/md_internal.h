@@ -97,6 +97,7 @@ struct LevelPlan {
     uint64_t per_chunk = 0;         // kind 0: ranks per lane
     std::vector<MEntry> mtab;       // kinds 2, 3
     int tc_q = 0;                   // kind 4: head size q (tail = the other g - q elements)
+    int tc_smin = 0;                // kind 4: combinations with c_{q+1} < tc_smin use (q+1)-heads
 };
 
 struct PlanOptions {
@@ -112,7 +113,9 @@ struct PlanOptions {
 // ---- tensor-core levels (md_tc.cu) ----
 size_t tc_tables_bytes(int k, int q, int W);  // head table of one matrix
 int tc_smem_bytes(int k, int W, int optin, int *with_bsub);
-uint64_t tc_level_items(int k, int g, int q, int W);
+uint64_t tc_level_items(int k, int g, int q, int smin, int W);
+int tc_split_point(int k, int q);   // s_min of the two-phase split (see md_tc.cu)
+size_t tc_heads_bytes(uint64_t nheads, int W);
 int tc_auto_head(int k, int W);     // q used when PlanOptions::tensor_head is 0
 int tc_max_upper();                 // largest g - q - 1 the tensor-core kernel handles
 
@@ -220,10 +223,11 @@ double estimate_work(const Code &c, int *d_est, int *g_stop);
 int launch_h2_build(const uint32_t *rows, uint32_t *h2, int k, int WP, void *stream);
 // Tables of Gamma_j for its tensor-core levels (tc_tables_bytes(k, q, W) bytes, 16-byte aligned).
 int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, int k, int q, int W, int WP,
-                     unsigned char *tables, void *stream);
+                     uint64_t nheads, unsigned char *tables, void *stream);
 // One tensor-core level: `blocks` persistent blocks (one per SM), work items from st->ctr[level].
-int launch_tc_level(const unsigned char *tables, const uint32_t *rows, const unsigned long long *binom_d, DevState *st,
-                    int k, int g, int q, int base, int level, int W, int WP, int check_stop, int blocks, void *stream);
+int launch_tc_level(const unsigned char *tables, const unsigned char *tables2, int smin, const uint32_t *rows,
+                    const unsigned long long *binom_d, DevState *st, int k, int g, int q, int base, int level, int W,
+                    int WP, int check_stop, int blocks, void *stream);
 int launch_level(const LevelArgs &a, int kind, int W, int WP, int blocks, int threads, size_t smem,
                  void *stream);
 int launch_finalize(const LevelArgs &a, void *stream);

@@ -13,6 +13,13 @@
 // colex rank is (head index) + sum_{i > q} C(c_i, i), so within one tail the first column
 // holding a row's best weight is that tail's smallest rank of it.
 //
+// Two phases cover a level: phase 0 takes the combinations with s = c_{q+1} >= s_min and the
+// split above; phase 1 takes those with c_{q+1} < s_min and splits one element later: heads
+// (c_1..c_{q+1}) with c_{q+1} < s_min (a colex prefix of the (q+1)-subsets) and tails
+// (c_{q+2}..c_g).  For small s the q-heads are few, so a tail would serve only one or two
+// head slices and cost more to produce than to multiply; the second phase gives every tail
+// of those combinations C(min(s, s_min), q + 1) heads.
+//
 //   * Heads: a table of the C(k, q) head sums as e4m3 signs (+1.0 = 0x38, -1.0 = 0xB8), in
 //     256-row slices of 8-row x 16-byte core matrices (the K-major operand layout without
 //     swizzle), built once per matrix and copied slice by slice into shared memory with bulk
@@ -97,6 +104,7 @@ struct TcItem {
     int na;                                // tail tiles: ceil(nt / 128); tile a row r = tail t0 + r na + a
     int u;                                 // U when the item was handed out
     int end;                               // 1: the level has no more items
+    int ph;                                // phase: heads of q + ph elements
 };
 
 // Heads of slice sl that belong to s (the MMA N covers them rounded up to 16).
@@ -112,7 +120,7 @@ struct TcShared {
     unsigned long long ifull[kRing];       // scheduler -> readers
     unsigned long long ifree[kRing];       // readers -> scheduler (11 warp arrivals)
     TcItem ring[kRing];
-    unsigned long long cum[kMaxN + 1];     // work items before s
+    unsigned long long cum[2][kMaxN + 1];  // per phase: work items before s
     uint32_t taddr;
     int abort;
     int stop;
@@ -323,12 +331,13 @@ __device__ __forceinline__ void sign_word(uint32_t x, uint32_t base, uint4 &lo, 
 
 // ------------------------------------------------------------------- tail walking ----
 struct TcArgs {
-    const unsigned char *heads;            // head slices (launch_tc_tables)
+    const unsigned char *heads[2];         // per phase: head slices (launch_tc_tables)
     const uint32_t *rows;                  // k x WP packed rows of Gamma_j
     const unsigned long long *binom;       // (k + 1) x (k + 1)
     DevState *st;
     int k, g, q, base, level, WP, tiles, check_stop;   // tiles: tail tiles per set
     int bsub;                              // 1: C(x, i), i <= kMaxV, staged in shared memory
+    int smin;                              // phase split (q: no second phase)
 };
 
 __device__ __forceinline__ unsigned long long C(const TcArgs &a, int n, int r) {
@@ -376,25 +385,31 @@ __device__ __forceinline__ void tail_unrank(const TcArgs &a, const unsigned long
     }
 }
 
-// Rank contribution of the tail with index t: C(s, q + 1) + sum_i C(o_i, q + 2 + i).
-__device__ __forceinline__ unsigned long long tail_rank_at(const TcArgs &a, int s, unsigned long long t) {
-    const int v = a.g - a.q - 1;
+// Rank contribution of the tail with index t of phase ph (heads of q = a.q + ph elements):
+// C(s, q + 1) + sum_i C(o_i, q + 2 + i).
+__device__ __forceinline__ unsigned long long tail_rank_at(const TcArgs &a, int ph, int s, unsigned long long t) {
+    const int q = a.q + ph, v = a.g - q - 1;
     int top = a.k - 2 - s;
-    unsigned long long r = C(a, s, a.q + 1);
+    unsigned long long r = C(a, s, q + 1);
     for (int i = v; i >= 1; i--) {
         const int x = colex_digit(a, i - 1, top, i, t);
         t -= C(a, x, i);
         top = x - 1;
-        r += C(a, x + s + 1, a.q + 1 + i);
+        r += C(a, x + s + 1, q + 1 + i);
     }
     return r;
 }
 
-// Items of s: groups of up to kGroup head slices x runs of 128 * tiles tails.
-__device__ __forceinline__ unsigned long long items_of(const TcArgs &a, int s) {
-    const int v = a.g - a.q - 1;
-    if (s < a.q || s > a.k - 1 - v) return 0;
-    const unsigned long long nb = C(a, s, a.q), nt = C(a, a.k - 1 - s, v);
+// Heads of s in phase ph: C(s, q) in phase 0 (s >= s_min), C(min(s, s_min), q + 1) in phase 1.
+__device__ __forceinline__ unsigned long long heads_of(const TcArgs &a, int ph, int s) {
+    return ph ? C(a, min(s, a.smin), a.q + 1) : C(a, s, a.q);
+}
+
+// Items of s in phase ph: groups of up to kGroup head slices x runs of 128 * tiles tails.
+__device__ __forceinline__ unsigned long long items_of(const TcArgs &a, int ph, int s) {
+    const int q = a.q + ph, v = a.g - q - 1;
+    if (v < 0 || s < (ph ? q : max(a.q, a.smin)) || s > a.k - 1 - v) return 0;
+    const unsigned long long nb = heads_of(a, ph, s), nt = C(a, a.k - 1 - s, v);
     const unsigned long long per = (unsigned long long)kTcM * a.tiles;
     const unsigned long long nsl = (nb + kTcN - 1) / kTcN;
     return ((nsl + kGroup - 1) / kGroup) * ((nt + per - 1) / per);
@@ -427,7 +442,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     DevState *st = a.st;
-    const int k = a.k, q = a.q, v = a.g - a.q - 1;
+    const int k = a.k;
     volatile int *abort_flag = &sh.abort;
 
     if (threadIdx.x == 0) {
@@ -460,14 +475,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             if (x < k) acc ^= __ldg(a.rows + x * a.WP + w);
         }
     }
-    for (int s = threadIdx.x; s < k; s += blockDim.x) sh.cum[s + 1] = items_of(a, s);
+    for (int i = threadIdx.x; i < 2 * k; i += blockDim.x) sh.cum[i / k][i % k + 1] = items_of(a, i / k, i % k);
     if (bsub)
         for (int i = threadIdx.x; i < (k + 1) * (kMaxV + 1); i += blockDim.x)
             bsub[i] = C(a, i / (kMaxV + 1), i % (kMaxV + 1));
     __syncthreads();
     if (threadIdx.x == 0) {
-        sh.cum[0] = 0;
-        for (int s = 0; s < k; s++) sh.cum[s + 1] += sh.cum[s];
+        for (int ph = 0; ph < 2; ph++) {
+            sh.cum[ph][0] = 0;
+            for (int s = 0; s < k; s++) sh.cum[ph][s + 1] += sh.cum[ph][s];
+        }
     }
     __syncthreads();
     if (sh.stop) return;
@@ -486,7 +503,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
     if (warp == kSchedWarp) {
         // ------------------------------------------------------------ scheduler ----
         if (lane == 0) {
-            const unsigned long long total = sh.cum[k];
+            const unsigned long long total0 = sh.cum[0][k], total = total0 + sh.cum[1][k];
             const unsigned long long per = (unsigned long long)kTcM * T;
             for (long long n = 0;; n++) {
                 const int slot = (int)(n % kRing);
@@ -494,25 +511,29 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                 if (use >= 1 && !mbar_wait(saddr(&sh.ifree[slot]), (use - 1) & 1, abort_flag)) break;
                 TcItem it{};
                 for (;;) {
-                    const unsigned long long idx = atomicAdd(&st->ctr[a.level], 1ull);
+                    unsigned long long idx = atomicAdd(&st->ctr[a.level], 1ull);
                     if (idx >= total) { it.end = 1; break; }
+                    const int ph = idx >= total0 ? 1 : 0;
+                    if (ph) idx -= total0;
+                    const unsigned long long *cum = sh.cum[ph];
                     int lo = 0, hi = k - 1;                    // last s with cum[s] <= idx
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) >> 1;
-                        if (sh.cum[mid] <= idx) lo = mid; else hi = mid - 1;
+                        if (cum[mid] <= idx) lo = mid; else hi = mid - 1;
                     }
                     const int s = lo;
-                    const unsigned long long local = idx - sh.cum[s];
-                    const unsigned long long nb = C(a, s, q);
+                    const unsigned long long local = idx - cum[s];
+                    const unsigned long long nb = heads_of(a, ph, s);
                     const unsigned long long nsl = (nb + kTcN - 1) / kTcN;
                     const unsigned long long ngr = (nsl + kGroup - 1) / kGroup;
                     const unsigned long long grp = local % ngr, tblock = local / ngr;
                     it.s = s;
+                    it.ph = ph;
                     it.nb = (int)nb;
                     it.sl0 = (int)(grp * kGroup);
                     it.nsl = (int)min((unsigned long long)kGroup, nsl - grp * kGroup);
                     it.t0 = tblock * per;
-                    it.nt = (int)min(per, C(a, k - 1 - s, v) - it.t0);
+                    it.nt = (int)min(per, C(a, k - 1 - s, a.g - a.q - ph - 1) - it.t0);
                     it.na = (it.nt + kTcM - 1) / kTcM;
                     const int U = (int)*(volatile unsigned int *)&st->U;
                     it.u = U;
@@ -521,7 +542,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                     if (a.check_stop && U <= *(volatile int *)&st->L) {
                         const unsigned long long key = *(volatile unsigned long long *)&st->key[a.level];
                         if (key != kNoKey && (int)(key >> kRankBits) == U &&
-                            (unsigned long long)it.sl0 * kTcN + tail_rank_at(a, s, it.t0) > (key & (kRankLimit - 1))) {
+                            (unsigned long long)it.sl0 * kTcN + tail_rank_at(a, ph, s, it.t0) > (key & (kRankLimit - 1))) {
                             atomicAdd(&st->skipped, 1ull);
                             continue;
                         }
@@ -552,7 +573,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                 const int buf = (int)(step & 1);
                 const int npad = (slice_heads(it, sl) + 15) & ~15;
                 const uint32_t bytes = (uint32_t)(npad / 8) * Cfg::kSbo;
-                const unsigned char *src = a.heads + (size_t)sl * Cfg::kBTile;
+                const unsigned char *src = a.heads[it.ph] + (size_t)sl * Cfg::kBTile;
                 mbar_expect_tx(saddr(&sh.bfull[buf]), bytes);
                 bulk_g2s(saddr(Btile + buf * Cfg::kBTile), src, bytes, saddr(&sh.bfull[buf]));
                 pend_buf = buf;
@@ -648,13 +669,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             n++;
             if (it.end) break;
             const int set = (int)(j & 1);
-            if (j >= 2 && !warp_wait(saddr(&sh.afree[set]), (unsigned)((j >> 1) - 1) & 1, abort_flag)) break;
+            const int v = a.g - a.q - it.ph - 1;               // upper elements of this item's tails
             {
                 // thread p walks tails [2 na p, 2 na p + 2 na): the first na go to tile row p,
                 // the next na to row p + 64 (tile t of each)
                 const int p = (warp - kProdWarp0) * 32 + lane;
                 const int first = 2 * it.na * p;
                 const int cnt = max(0, min(2 * it.na, it.nt - first));
+                // the first tail needs no tile memory: it is found while the set is still in use
 #pragma unroll
                 for (int i = 0; i < NW; i++) Sx[i] = 0;
                 if (cnt > 0) {
@@ -664,6 +686,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                     for (int i = 0; i < kMaxV; i++)
                         if (i < v) xor_words<NW>(Sx, rT, k, o[i], w0, W);
                 }
+                if (j >= 2 && !warp_wait(saddr(&sh.afree[set]), (unsigned)((j >> 1) - 1) & 1, abort_flag)) break;
                 for (int m = 0; m < 2 * it.na; m++) {
                     const int r = m < it.na ? p : p + 64;
                     const int t = m < it.na ? m : m - it.na;
@@ -787,7 +810,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                         if (pass) {
                             const int w = a.base + (32 * W - (int)mx) / 2;
                             const unsigned long long rank = (unsigned long long)(p0 + 128 * half + firstc) +
-                                                            tail_rank_at(a, it.s, it.t0 + (unsigned long long)row);
+                                                            tail_rank_at(a, it.ph, it.s, it.t0 + (unsigned long long)row);
                             atomicMin(&st->key[a.level], ((unsigned long long)w << kRankBits) | rank);
                             atomicMin(&st->U, (unsigned int)w);
                             ubest = min(ubest, w);
@@ -866,6 +889,8 @@ size_t head_bytes(int k, int q, int W) {
 
 size_t tc_tables_bytes(int k, int q, int W) { return head_bytes(k, q, W); }
 
+size_t tc_heads_bytes(uint64_t nheads, int W) { return (size_t)((nheads + kTcN - 1) / kTcN) * kTcN * 32 * W; }
+
 int tc_auto_head(int k, int W) {
     // three-element heads keep the head dimension of the product wide for every s that
     // carries much work; fall back to pairs when their table would be too large
@@ -890,22 +915,31 @@ int tc_smem_bytes(int k, int W, int optin, int *with_bsub) {
     return bytes < 116 * 1024 ? 116 * 1024 : bytes;
 }
 
-uint64_t tc_level_items(int k, int g, int q, int W) {
-    const int v = g - q - 1;
-    if (v < 0) return 0;
+int tc_split_point(int k, int q) {
+    // the smallest s whose q-heads fill seven slices: below it, tails of q-heads would serve
+    // too few heads, and the second phase's (q+1)-heads take over
+    int s = q;
+    while (s < k && binom(s, q) < 7ull * kTcN) s++;
+    return s;
+}
+
+uint64_t tc_level_items(int k, int g, int q, int smin, int W) {
     uint64_t total = 0;
     const uint64_t per = (uint64_t)kTcM * tc_tiles_per_set(W);
-    for (int s = q; s <= k - 1 - v; s++) {
-        const uint64_t nb = binom(s, q), nt = binom(k - 1 - s, v);
-        const uint64_t nsl = (nb + kTcN - 1) / kTcN;
-        total += ((nsl + kGroup - 1) / kGroup) * ((nt + per - 1) / per);
+    for (int ph = 0; ph < 2; ph++) {
+        const int qq = q + ph, v = g - qq - 1;
+        if (v < 0) continue;
+        for (int s = ph ? qq : std::max(q, smin); s <= k - 1 - v; s++) {
+            const uint64_t nb = ph ? binom(std::min(s, smin), qq) : binom(s, qq), nt = binom(k - 1 - s, v);
+            const uint64_t nsl = (nb + kTcN - 1) / kTcN;
+            total += ((nsl + kGroup - 1) / kGroup) * ((nt + per - 1) / per);
+        }
     }
     return total;
 }
 
 int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, int k, int q, int W, int WP,
-                     unsigned char *tables, void *stream) {
-    const uint64_t nheads = binom(k, q);
+                     uint64_t nheads, unsigned char *tables, void *stream) {
     const uint64_t nrows = (nheads + kTcN - 1) / kTcN * kTcN;
     if (nrows == 0) return 0;
     const uint64_t total = nrows * (uint64_t)W;
@@ -914,14 +948,16 @@ int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, in
     return (int)cudaGetLastError();
 }
 
-int launch_tc_level(const unsigned char *tables, const uint32_t *rows, const unsigned long long *binom_d, DevState *st,
-                    int k, int g, int q, int base, int level, int W, int WP, int check_stop, int blocks, void *stream) {
+int launch_tc_level(const unsigned char *tables, const unsigned char *tables2, int smin, const uint32_t *rows,
+                    const unsigned long long *binom_d, DevState *st, int k, int g, int q, int base, int level, int W,
+                    int WP, int check_stop, int blocks, void *stream) {
     int dev = 0, optin = 0, with_bsub = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return (int)cudaErrorInvalidValue;
     const size_t smem = (size_t)tc_smem_bytes(k, W, optin, &with_bsub);
-    TcArgs a{tables, rows, binom_d, st, k, g, q, base, level, WP, tc_tiles_per_set(W), check_stop, with_bsub};
+    TcArgs a{{tables, tables2}, rows, binom_d, st, k, g, q, base, level, WP, tc_tiles_per_set(W), check_stop,
+             with_bsub, smin};
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     switch (W) {
