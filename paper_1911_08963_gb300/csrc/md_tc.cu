@@ -36,13 +36,17 @@
 //     so the producers fill one while the other is in use) times a group of up to 16 head
 //     slices of the same s: every tail tile is multiplied with each slice of the group, so
 //     generating it costs little per codeword, and each slice is fetched once for T tiles.
-//   * One thread issues tcgen05.mma kind::f8f6f4 (M = 128 tails, N <= 256 heads, one
-//     instruction per 32 packed bits); D accumulates in fp32 in tensor memory (exact, |D| <=
-//     256), two accumulators of 256 columns so the next product overlaps the epilogue.
-//   * Eight epilogue warps (two per tensor-memory lane quarter, one per half of the columns)
-//     read D with tcgen05.ld.red, which also returns each lane's maximum over the columns
-//     it loads, so no per-element arithmetic is left; the four loads of a half are in flight
-//     together (one round trip per accumulator); a row reaching
+//   * Two threads issue tcgen05.mma kind::f8f6f4 (M = 128 tails, N <= 256 heads, one
+//     instruction per 32 packed bits), each into its own accumulator: D accumulates in fp32
+//     in tensor memory (exact, |D| <= 256), two accumulators of 256 columns.  The W MMAs of
+//     one product form a dependent chain; issued from two threads, the chains of the two
+//     accumulators interleave in the tensor pipe, which hides the latency between the MMAs
+//     of a chain, while the epilogue drains whichever accumulator is done.
+//   * Four epilogue warps (one per tensor-memory lane quarter) read D with tcgen05.ld.red,
+//     which also returns each lane's maximum over the columns it loads, so no per-element
+//     arithmetic is left: two round trips of four loads per accumulator.  (Two warps of a
+//     sub-partition issuing tcgen05.ld.red while products run slowed the turnaround of the
+//     accumulators, hence one warp per quarter.)  A row reaching
 //     K - 2 (min(U, best) - base) is resolved to (weight, first rank) and published with
 //     atomicMin, as in the other level kernels.
 //   * One scheduler thread takes work items (s, head slices, run of tails) from the level's
@@ -66,17 +70,19 @@ using namespace dev;
 
 constexpr int kTcM = 128;                  // tails per tile (tensor-memory lanes)
 constexpr int kTcN = 256;                  // heads per slice (accumulator columns)
-// 12 warps = 3 per SM sub-partition, so every thread can have 168 registers: an epilogue warp
-// then keeps a whole 128-column half of an accumulator (four loads) in flight at once.
-constexpr int kEpiWarps = 8;               // warps 0-7
-constexpr int kProdWarp0 = 8;              // warps 8-9: two tile rows per thread
+// 9 warps: an epilogue warp keeps four 32-column loads (a 128-column half of an accumulator)
+// in flight; the register cap leaves room for them without spills.
+constexpr int kEpiWarps = 4;               // warps 0-3: one per tensor-memory lane quarter
+constexpr int kProdWarp0 = 4;              // warps 4-5: two tile rows per thread
 constexpr int kProdWarps = 2;
-constexpr int kMmaWarp = 10;
-constexpr int kSchedWarp = 11;
-constexpr int kTcWarps = 12;
+constexpr int kMmaWarp0 = 6;              // warps 6-7: one MMA issuer per accumulator
+constexpr int kMmaWarps = 2;
+constexpr int kSchedWarp = 8;
+constexpr int kTcWarps = 9;
 constexpr int kTcThreads = kTcWarps * 32;
+constexpr int kTcMaxRegs = 200;
 constexpr int kRing = 8;                   // work items between the scheduler and the others
-constexpr int kItemReaders = kEpiWarps + kProdWarps + 1;   // warps that take each ring entry
+constexpr int kItemReaders = kEpiWarps + kProdWarps + kMmaWarps;   // warps that take each ring entry
 constexpr uint32_t kTmemCols = 512;
 constexpr unsigned long long kWaitNs = 4000000000ull;
 constexpr int kMaxV = 10;                  // upper elements of a tail (g - q - 1) handled
@@ -425,7 +431,7 @@ __device__ __forceinline__ void xor_words(uint32_t (&S)[NW], const uint32_t *tab
 
 // ------------------------------------------------------------------------ kernel ----
 template <int W>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
+__global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
     using Cfg = TcCfg<W>;
     constexpr int T = Cfg::kTiles;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -450,11 +456,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
         sh.stop = a.check_stop ? *(volatile int *)&st->stop : 0;
         for (int i = 0; i < 2; i++) {
             mbar_init(saddr(&sh.afull[i]), kProdWarps);
-            mbar_init(saddr(&sh.afree[i]), 1);
+            mbar_init(saddr(&sh.afree[i]), kMmaWarps);
             mbar_init(saddr(&sh.mdone[i]), 1);
             mbar_init(saddr(&sh.tfree[i]), kEpiWarps);
             mbar_init(saddr(&sh.bfull[i]), 1);
-            mbar_init(saddr(&sh.bfree[i]), 1);
+            mbar_init(saddr(&sh.bfree[i]), kMmaWarps);
         }
         for (int i = 0; i < kRing; i++) {
             mbar_init(saddr(&sh.ifull[i]), 1);
@@ -554,9 +560,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                 if (it.end) break;
             }
         }
-    } else if (warp == kMmaWarp) {
+    } else if (warp >= kMmaWarp0 && warp < kMmaWarp0 + kMmaWarps) {
         // ------------------------------------------------- MMA issue and head slices ----
+        // Two issuers walk the same items and slices; issuer `me` multiplies the tiles u with
+        // u % 2 == me into accumulator me.  A product of K = 32 W is a chain of W dependent
+        // MMAs; from two threads the tensor pipe interleaves the chains of both accumulators
+        // and hides the latency between the MMAs of a chain.  Issuer 0 also fetches the head
+        // slices; both release a slice buffer and a tail set (barriers of two arrivals).
         if (lane == 0) {
+            const int me = warp - kMmaWarp0;
             long long n = 0;                               // ring entries taken
             bool ok = true;
             auto take = [&](TcItem &it) -> bool {
@@ -586,7 +598,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             int last_acc = -1;
             unsigned last_parity = 0;
             ok = take(cur);
-            if (ok && !cur.end) load_slice(cur, cur.sl0, 0);
+            if (ok && !cur.end && me == 0) load_slice(cur, cur.sl0, 0);
             while (ok && !cur.end) {
                 const int set = (int)(j & 1);
                 if (!mbar_wait(saddr(&sh.afull[set]), (unsigned)(j >> 1) & 1, abort_flag)) { ok = false; break; }
@@ -606,11 +618,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                         ni = &nxt;
                         nsl_idx = nxt.sl0;
                     }
-                    bool fetched = ni->end != 0;
+                    bool fetched = ni->end != 0 || me != 0;
                     const uint32_t prev_free = saddr(&sh.bfree[(step + 1) & 1]);
                     const unsigned prev_parity = (unsigned)((step - 1) >> 1) & 1;
-                    for (int t = 0; t < cur.na; t++) {
+                    for (int t = 0; t < cur.na; t++, u++) {
                         const int acc = (int)(u & 1);
+                        if (acc != me) continue;
                         if (u >= 2 && !mbar_wait(saddr(&sh.tfree[acc]), ((u >> 1) - 1) & 1, abort_flag)) {
                             ok = false;
                             break;
@@ -625,7 +638,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                         mma_commit(saddr(&sh.mdone[acc]));
                         last_acc = acc;
                         last_parity = (u >> 1) & 1;
-                        u++;
                         if (!fetched && (step == 0 || mbar_poll(prev_free, prev_parity))) {
                             load_slice(*ni, nsl_idx, step + 1);
                             fetched = true;
@@ -734,9 +746,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
         }
     } else {
         // ------------------------------------------------------------- epilogue ----
-        const int quarter = warp & 3, half = warp >> 2;
+        const int quarter = warp;
         const int r = quarter * 32 + lane;                 // tensor-memory lane = tile row
-        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16);
         long long n = 0;
         unsigned u = 0;
         bool ok = true;
@@ -751,7 +763,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
             if (it.end) break;
             for (int sl = 0; sl < it.nsl && ok; sl++) {
                 const int p0 = (it.sl0 + sl) * kTcN;
-                const int nvh = max(0, min(128, slice_heads(it, it.sl0 + sl) - 128 * half));   // columns here
+                const int nvh = slice_heads(it, it.sl0 + sl);                                   // columns here
                 const int nchunk = (nvh + 31) >> 5;
                 for (int t = 0; t < it.na; t++) {
                     const int acc = (int)(u & 1);
@@ -759,16 +771,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                     tc_after();
                     const uint32_t col0 = lane_base + (uint32_t)(acc * kTcN);
                     float mx = -1e30f;
-                    if (nvh == 128) {
-                        // all four chunks whole: one round trip
-                        float v0[32], v1[32], v2[32], v3[32], r0, r1, r2, r3;
-                        tmem_ldmax32(col0, v0, r0);
-                        tmem_ldmax32(col0 + 32u, v1, r1);
-                        tmem_ldmax32(col0 + 64u, v2, r2);
-                        tmem_ldmax32(col0 + 96u, v3, r3);
-                        tmem_wait_red2(v0, r0, v1, r1);
-                        tmem_wait_red2(v2, r2, v3, r3);
-                        mx = fmax3(fmax3(r0, r1, r2), r3, mx);
+                    if (nvh == kTcN) {
+                        // all eight chunks whole: two round trips of four loads
+#pragma unroll 1
+                        for (int h = 0; h < 2; h++) {
+                            float v0[32], v1[32], v2[32], v3[32], r0, r1, r2, r3;
+                            tmem_ldmax32(col0 + 128u * h, v0, r0);
+                            tmem_ldmax32(col0 + 128u * h + 32u, v1, r1);
+                            tmem_ldmax32(col0 + 128u * h + 64u, v2, r2);
+                            tmem_ldmax32(col0 + 128u * h + 96u, v3, r3);
+                            tmem_wait_red2(v0, r0, v1, r1);
+                            tmem_wait_red2(v2, r2, v3, r3);
+                            mx = fmax3(fmax3(r0, r1, r2), r3, mx);
+                        }
                     } else
                     for (int c = 0; c < nchunk; c += 2) {
                         const bool two = c + 1 < nchunk;
@@ -809,7 +824,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_kernel(const TcArgs a) {
                         }
                         if (pass) {
                             const int w = a.base + (32 * W - (int)mx) / 2;
-                            const unsigned long long rank = (unsigned long long)(p0 + 128 * half + firstc) +
+                            const unsigned long long rank = (unsigned long long)(p0 + firstc) +
                                                             tail_rank_at(a, it.ph, it.s, it.t0 + (unsigned long long)row);
                             atomicMin(&st->key[a.level], ((unsigned long long)w << kRankBits) | rank);
                             atomicMin(&st->U, (unsigned int)w);
