@@ -70,8 +70,10 @@ using namespace dev;
 
 constexpr int kTcM = 128;                  // tails per tile (tensor-memory lanes)
 constexpr int kTcN = 256;                  // heads per slice (accumulator columns)
-// 9 warps: an epilogue warp keeps four 32-column loads (a 128-column half of an accumulator)
-// in flight; the register cap leaves room for them without spills.
+// 9 warps: one SM sub-partition holds three of them, and its 16384 registers cap a thread at
+// 170, so 168 with the allocation unit of 8; a launch above the cap fails for lack of
+// registers, hence the explicit limit.  An epilogue warp keeps four 32-column loads (a
+// 128-column half of an accumulator) in flight within it.
 constexpr int kEpiWarps = 4;               // warps 0-3: one per tensor-memory lane quarter
 constexpr int kProdWarp0 = 4;              // warps 4-5: two tile rows per thread
 constexpr int kProdWarps = 2;
@@ -80,7 +82,7 @@ constexpr int kMmaWarps = 2;
 constexpr int kSchedWarp = 8;
 constexpr int kTcWarps = 9;
 constexpr int kTcThreads = kTcWarps * 32;
-constexpr int kTcMaxRegs = 200;
+constexpr int kTcMaxRegs = 168;
 constexpr int kRing = 8;                   // work items between the scheduler and the others
 constexpr int kItemReaders = kEpiWarps + kProdWarps + kMmaWarps;   // warps that take each ring entry
 constexpr uint32_t kTmemCols = 512;
