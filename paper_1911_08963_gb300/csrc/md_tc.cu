@@ -24,10 +24,11 @@
 //     256-row slices of 8-row x 16-byte core matrices (the K-major operand layout without
 //     swizzle), built once per matrix and copied slice by slice into shared memory with bulk
 //     copies (cp.async.bulk, completion on an mbarrier).
-//   * Tails: two producer warps, two tile rows per thread; a thread unranks one tail per
-//     item and walks its 2 na consecutive tails in colex order (the first na fill its first
-//     row across the item's tiles, the rest its second row), keeping the tail sum in
-//     registers, and writes its e4m3 signs: two 16-byte stores per packed word.  A colex step moves a run of consecutive elements
+//   * Tails: four producer warps (one per SM sub-partition, so their work spreads evenly
+//     beside the epilogue warps), one tile row per thread; a thread unranks one tail per
+//     item and walks its na consecutive tails in colex order (row p of each of the item's
+//     tiles), keeping the tail sum in registers, and writes its e4m3 signs: two 16-byte
+//     stores per packed word.  A colex step moves a run of consecutive elements
 //     o0..o0+m: they leave, s+1..s+m and o0+m+1 enter, which prefix XORs of the rows give in
 //     five lookups whatever m is (usually m = 0: one XOR with the difference of two adjacent
 //     rows).  The rows, their adjacent differences and prefix XORs sit in shared memory
@@ -70,17 +71,18 @@ using namespace dev;
 
 constexpr int kTcM = 128;                  // tails per tile (tensor-memory lanes)
 constexpr int kTcN = 256;                  // heads per slice (accumulator columns)
-// 9 warps: one SM sub-partition holds three of them, and its 16384 registers cap a thread at
+// 11 warps: one SM sub-partition holds three of them, and its 16384 registers cap a thread at
 // 170, so 168 with the allocation unit of 8; a launch above the cap fails for lack of
 // registers, hence the explicit limit.  An epilogue warp keeps four 32-column loads (a
 // 128-column half of an accumulator) in flight within it.
 constexpr int kEpiWarps = 4;               // warps 0-3: one per tensor-memory lane quarter
-constexpr int kProdWarp0 = 4;              // warps 4-5: two tile rows per thread
-constexpr int kProdWarps = 2;
-constexpr int kMmaWarp0 = 6;              // warps 6-7: one MMA issuer per accumulator
+constexpr int kProdWarp0 = 4;              // warps 4-7: one tile row per thread
+constexpr int kProdWarps = 4;
+constexpr int kProdRows = kTcM / (32 * kProdWarps);   // tile rows per producer thread
+constexpr int kMmaWarp0 = 8;              // warps 8-9: one MMA issuer per accumulator
 constexpr int kMmaWarps = 2;
-constexpr int kSchedWarp = 8;
-constexpr int kTcWarps = 9;
+constexpr int kSchedWarp = 10;
+constexpr int kTcWarps = 11;
 constexpr int kTcThreads = kTcWarps * 32;
 constexpr int kTcMaxRegs = 168;
 constexpr int kRing = 8;                   // work items between the scheduler and the others
@@ -685,11 +687,12 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
             const int set = (int)(j & 1);
             const int v = a.g - a.q - it.ph - 1;               // upper elements of this item's tails
             {
-                // thread p walks tails [2 na p, 2 na p + 2 na): the first na go to tile row p,
-                // the next na to row p + 64 (tile t of each)
+                // thread p walks tails [R na p, R na p + R na), R = kProdRows rows per thread:
+                // the first na go to tile row p (tile t of each), the next na to row
+                // p + 128 / R, and so on
                 const int p = (warp - kProdWarp0) * 32 + lane;
-                const int first = 2 * it.na * p;
-                const int cnt = max(0, min(2 * it.na, it.nt - first));
+                const int first = kProdRows * it.na * p;
+                const int cnt = max(0, min(kProdRows * it.na, it.nt - first));
                 // the first tail needs no tile memory: it is found while the set is still in use
 #pragma unroll
                 for (int i = 0; i < NW; i++) Sx[i] = 0;
@@ -701,9 +704,9 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                         if (i < v) xor_words<NW>(Sx, rT, k, o[i], w0, W);
                 }
                 if (j >= 2 && !warp_wait(saddr(&sh.afree[set]), (unsigned)((j >> 1) - 1) & 1, abort_flag)) break;
-                for (int m = 0; m < 2 * it.na; m++) {
-                    const int r = m < it.na ? p : p + 64;
-                    const int t = m < it.na ? m : m - it.na;
+                for (int m = 0; m < kProdRows * it.na; m++) {
+                    const int r = p + (kTcM / kProdRows) * (m / it.na);
+                    const int t = m % it.na;
                     unsigned char *rowp = Atile + (set * T + t) * Cfg::kATile + (r >> 3) * Cfg::kSbo + (r & 7) * 16;
                     const bool valid = m < cnt;
 #pragma unroll
@@ -807,8 +810,9 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                             mx = fmax3(mx, chunk_max(va, nvh - 32 * c), chunk_max(vb, two ? nvh - 32 * (c + 1) : 32));
                         }
                     }
-                    // tail index within the item: row r of tile t is tail 2 na (r mod 64) + na (r / 64) + t
-                    const int row = 2 * it.na * (r & 63) + it.na * (r >> 6) + t;
+                    // tail index within the item: row r of tile t is tail R na (r mod 128 / R) +
+                    // na (r div 128 / R) + t, R = kProdRows (na r + t with one row per thread)
+                    const int row = kProdRows * it.na * (r % (kTcM / kProdRows)) + it.na * (r / (kTcM / kProdRows)) + t;
                     const int thr = min(it.u, ubest) - a.base;
                     const bool pass = row < it.nt && thr >= 0 && mx >= (float)(32 * W - 2 * thr);
                     if (__any_sync(kFull, pass)) {
