@@ -183,12 +183,15 @@ int md_scan_range(md_handle h, int g, int j, uint64_t r0, uint64_t r1, int bound
 int md_scan_task(md_handle h, int g, int j, int M, uint64_t u0, uint64_t u1, int bound,
                  int *weight, uint64_t *first_rank);
 
-/* The work decomposition of level (g, j) that md_compute uses (host-only, no device
-   work).  *kind: 0 = per-lane colex rank ranges (small levels), 2 or 3 = the head size P
-   of the split enumeration.  For kind 2/3 each entry i describes the tasks with
-   c_{P+1} = M: tasks[i] = {M, number of upper parts, upper parts per lane, first work
-   item}; *count receives the number of entries (at most max written); for kind 0,
-   *count = 0.  *work_items receives the number of work items of the level. */
+/* The work decomposition of level (g, j) that md_compute uses under the handle's options
+   (host-only, no device work).  *kind: 0 = per-lane colex rank ranges (small levels), 2 or
+   3 = the head size P of the split enumeration, 4 = the tensor-core product (heads of q
+   elements, q = md_options.tensor_head or 3, and for small c_{q+1} of q + 1 elements).
+   For kind 2/3 each entry i describes the tasks with c_{P+1} = M: tasks[i] = {M, number
+   of upper parts, upper parts per lane, first work item}; *count receives the number of
+   entries (at most max written); for kinds 0 and 4, *count = 0.  *work_items receives the
+   number of work items of the level (kind 4: groups of up to 16 slices of 256 heads times
+   runs of up to 128 T tails, T = 8, 4, 2, 1 for packed widths W <= 2, 4, 6, 8). */
 typedef struct md_task_info {
     uint32_t M;
     uint32_t per_lane;

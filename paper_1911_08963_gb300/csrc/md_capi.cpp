@@ -519,6 +519,8 @@ int md_level_plan(md_handle h, int g, int j, int *kind, md_task_info *tasks, int
     po.chunk_log2 = h->opt.chunk_log2 > 0 ? h->opt.chunk_log2 : 20;
     po.filter = h->opt.filter;
     po.stop_rule = h->opt.stop_rule;
+    po.tensor = h->opt.tensor;
+    po.tensor_head = h->opt.tensor_head;
     LevelPlan p = plan_level(c, g, j, po);
     *kind = p.kind;
     *work_items = p.nchunks;

@@ -105,10 +105,11 @@ def test_gamma_textbook(B):
 def test_level_plan_covers_every_combination(B, n, k, g):
     """The split decomposition covers C(k, g) combinations: sum over M of
     C(k-1-M, v) upper parts times C(M, P) heads (closed form), work items are contiguous,
-    and every work item holds at most 32 lanes x per_lane upper parts."""
+    and every work item holds at most 32 lanes x per_lane upper parts.  (tensor = 0: the
+    popcount kernels' plan, which large levels use without the tensor cores.)"""
     import math
     rows = T.random_rows(n, k, 3)
-    h = B.md_create(T.pack(rows, n), n, k)
+    h = B.md_create(T.pack(rows, n), n, k, B.md_options_init(tensor=0))
     try:
         kind, tasks, items = B.md_level_plan(h, g, 0)
         if g <= 4:
@@ -129,6 +130,50 @@ def test_level_plan_covers_every_combination(B, n, k, g):
         assert total == math.comb(k, g)
     finally:
         B.md_destroy(h)
+
+
+def _tc_items(k, g, q, W):
+    """Work items of a tensor-core level and the combinations they cover, restated from the
+    two-phase split: phase 0 takes c_{q+1} = s >= s_min with the C(s, q) q-heads below s,
+    phase 1 takes c_{q+1} < s_min with (q+1)-heads below min(c_{q+2}, s_min); each s is
+    cut into groups of up to 16 slices of 256 heads times runs of up to 128 T tails."""
+    import math
+    T_ = 8 if W <= 2 else 4 if W <= 4 else 2 if W <= 6 else 1
+    smin = q
+    if g >= q + 2:
+        while smin < k and math.comb(smin, q) < 7 * 256:
+            smin += 1
+    items = cover = 0
+    for ph in (0, 1):
+        qq, v = q + ph, g - q - ph - 1
+        if v < 0:
+            continue
+        for s in range(qq if ph else max(q, smin), k - v):
+            nb = math.comb(min(s, smin), qq) if ph else math.comb(s, qq)
+            nt = math.comb(k - 1 - s, v)
+            items += -(-(-(-nb // 256)) // 16) * -(-nt // (128 * T_))
+            cover += nb * nt
+    return items, cover
+
+
+@pytest.mark.parametrize("n,k,g,head,tensor", [(200, 100, 8, 0, 1), (200, 100, 10, 0, 1), (128, 64, 7, 0, 1),
+                                               (256, 60, 6, 0, 2), (100, 33, 4, 3, 2), (120, 40, 6, 2, 2),
+                                               (90, 30, 9, 0, 2)])
+def test_level_plan_tensor_items(B, n, k, g, head, tensor):
+    """Levels md_compute runs on the tensor cores report kind 4; the item count matches the
+    two-phase split restated here, and the two phases cover the C(k, g) combinations once."""
+    import math
+    h = B.md_create(T.pack(T.random_rows(n, k, 5), n), n, k, B.md_options_init(tensor=tensor, tensor_head=head))
+    try:
+        kind, tasks, items = B.md_level_plan(h, g, 0)
+    finally:
+        B.md_destroy(h)
+    q = head or 3
+    W = -(-(n - k) // 32)
+    want, cover = _tc_items(k, g, q, W)
+    assert kind == 4 and tasks == []
+    assert items == want
+    assert cover == math.comb(k, g)
 
 
 def test_level_plan_small_enumeration_exact(B):
