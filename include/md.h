@@ -103,6 +103,11 @@ typedef struct md_options {
                                  integer results); 0 = never; 2 = every level with g >= q + 1
                                  (a test setting).  Results are identical for all. */
     int tensor_head;          /* head size q of the tensor-core split (2 or 3); 0 = automatic */
+    int test_stall;           /* test hook, 0 in normal use.  1 = in every tensor-core level the
+                                 tail producers never signal their first tile set, so the
+                                 MMA issuers' bounded wait (4 s) runs out: each block frees
+                                 its tensor memory and returns, the run stops, and
+                                 md_compute returns MD_ETIMEOUT with the context intact */
 } md_options;
 
 /* Result details of the last md_compute on a handle. */

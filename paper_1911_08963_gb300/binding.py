@@ -31,7 +31,7 @@ class md_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("cancel_flag", ctypes.POINTER(ctypes.c_int)),
                 ("batch_mode", ctypes.c_int), ("use_graph", ctypes.c_int), ("plan_horizon", ctypes.c_int),
                 ("stop_rule", ctypes.c_int), ("perm_trials", ctypes.c_int), ("perm_seed", ctypes.c_uint64),
-                ("tensor", ctypes.c_int), ("tensor_head", ctypes.c_int)]
+                ("tensor", ctypes.c_int), ("tensor_head", ctypes.c_int), ("test_stall", ctypes.c_int)]
 
 
 class md_info(ctypes.Structure):

@@ -227,7 +227,7 @@ int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, in
 // One tensor-core level: `blocks` persistent blocks (one per SM), work items from st->ctr[level].
 int launch_tc_level(const unsigned char *tables, const unsigned char *tables2, int smin, const uint32_t *rows,
                     const unsigned long long *binom_d, DevState *st, int k, int g, int q, int base, int level, int W,
-                    int WP, int check_stop, int blocks, void *stream);
+                    int WP, int check_stop, int blocks, int stall, void *stream);
 int launch_level(const LevelArgs &a, int kind, int W, int WP, int blocks, int threads, size_t smem,
                  void *stream);
 int launch_finalize(const LevelArgs &a, void *stream);

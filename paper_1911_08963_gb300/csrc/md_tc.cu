@@ -348,6 +348,7 @@ struct TcArgs {
     int k, g, q, base, level, WP, tiles, check_stop;   // tiles: tail tiles per set
     int bsub;                              // 1: C(x, i), i <= kMaxV, staged in shared memory
     int smin;                              // phase split (q: no second phase)
+    int stall;                             // test hook: the first tile set is never signalled
 };
 
 __device__ __forceinline__ unsigned long long C(const TcArgs &a, int n, int r) {
@@ -746,7 +747,7 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
             }
             fence_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(saddr(&sh.afull[set]));
+            if (lane == 0 && !(a.stall && j == 0)) mbar_arrive(saddr(&sh.afull[set]));
             j++;
         }
     } else {
@@ -846,7 +847,11 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
         }
     }
 
-    if (sh.abort && threadIdx.x == 0) atomicExch(&st->error, MD_ETIMEOUT);
+    if (sh.abort && threadIdx.x == 0) {
+        // a wait ran out: record it and stop the run (the levels after this one return at once)
+        atomicExch(&st->error, MD_ETIMEOUT);
+        atomicExch(&st->stop, 1);
+    }
     tc_before();
     __syncthreads();
     if (warp == 0) {
@@ -971,14 +976,14 @@ int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, in
 
 int launch_tc_level(const unsigned char *tables, const unsigned char *tables2, int smin, const uint32_t *rows,
                     const unsigned long long *binom_d, DevState *st, int k, int g, int q, int base, int level, int W,
-                    int WP, int check_stop, int blocks, void *stream) {
+                    int WP, int check_stop, int blocks, int stall, void *stream) {
     int dev = 0, optin = 0, with_bsub = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return (int)cudaErrorInvalidValue;
     const size_t smem = (size_t)tc_smem_bytes(k, W, optin, &with_bsub);
     TcArgs a{{tables, tables2}, rows, binom_d, st, k, g, q, base, level, WP, tc_tiles_per_set(W), check_stop,
-             with_bsub, smin};
+             with_bsub, smin, stall};
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     switch (W) {

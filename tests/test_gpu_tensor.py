@@ -147,3 +147,20 @@ def test_tensor_mid_level_stop(B):
     res = oracle_cached(G, 100, 33, (100, 33, 41))
     info = assert_parity(B, G, 100, 33, res, tensor=2)
     assert info["skipped_work"] >= 0
+
+
+def test_tensor_wait_timeout_is_reported(B):
+    """Failure detection without a fault: with the test hook set, the tail producers never
+    signal their first tile set, every block's bounded wait runs out (4 s), frees its tensor
+    memory and returns, the run stops, and md_compute reports MD_ETIMEOUT; the context stays
+    usable and the next run is exact."""
+    G, n, k = I.single_code("rand64x32")
+    res = oracle_cached(G, n, k, "rand64x32")
+    h = B.md_create(G, n, k, B.md_options_init(tensor=2, test_stall=1))
+    try:
+        with pytest.raises(B.MDError) as e:
+            B.md_compute(h, n)
+        assert e.value.code == 8                       # MD_ETIMEOUT
+    finally:
+        B.md_destroy(h)
+    assert_parity(B, G, n, k, res, tensor=2)
