@@ -116,14 +116,16 @@ def test_rand200x100_stage6_tensor(B):
     assert d == res.d
 
 
-def test_tensor_matches_split_kernel_stage8(B):
-    """Consistency at the benchmark's matrix size, beyond the oracle's reach: the records of the
-    tensor-core levels g = 7, 8 equal those of the popcount kernel (itself pinned to the
-    oracle by sampled tasks), and each record's codeword has the recorded weight."""
+def test_tensor_matches_split_kernel_stage10(B):
+    """Consistency at the benchmark's configuration ([200,100] seed 3, stages g <= 10, the
+    launches bench.py times), beyond the oracle's reach for whole levels: the records of the
+    tensor-core levels g = 6..10 equal those of the popcount kernels (themselves pinned to
+    the oracle by sampled tasks), and each record's codeword has the recorded weight."""
     G, n, k = I.single_code("rand200x100")
-    _, _, _, lev_tc = run_gpu(B, G, n, k, max_stage=8, tensor=1)
-    _, _, _, lev_pc = run_gpu(B, G, n, k, max_stage=8, tensor=0)
+    _, _, _, lev_tc = run_gpu(B, G, n, k, max_stage=10, tensor=1)
+    _, _, _, lev_pc = run_gpu(B, G, n, k, max_stage=10, tensor=0)
     assert lev_tc == lev_pc
+    assert max(lv[0] for lv in lev_tc) == 10
     opt = B.md_options_init()
     h = B.md_create(G, n, k, opt)
     try:
@@ -138,6 +140,35 @@ def test_tensor_matches_split_kernel_stage8(B):
         for c in comb:
             row ^= gam[j][c]
         assert sum(bin(int(x)).count("1") for x in row) == w
+
+
+def test_tensor_stage10_record_is_window_minimum(B):
+    """Sampled outputs at full size: for each level (10, j) the oracle scans colex-rank
+    windows one combination at a time (the first ranks, ranks ending at the record, and
+    windows spread over the level); no codeword there is lighter than the level's record,
+    and the record's own rank has the recorded weight."""
+    import math
+    G, n, k = I.single_code("rand200x100")
+    gams, _, _ = O.gammas(G, n, k)
+    d, _, _, levels = run_gpu(B, G, n, k, max_stage=10)
+    total = math.comb(k, 10)
+    span = 1 << 23
+    checked = 0
+    for g, j, w, first, count in levels:
+        if g != 10:
+            continue
+        checked += 1
+        starts = [0] + [(total // 5) * i for i in range(1, 5)]
+        if w >= 0:
+            starts.append(max(0, first + 1 - span))
+        for r0 in starts:
+            r1 = min(total, r0 + span)
+            wmin, rmin = O.scan(gams[j], n, k, g, r0, r1, threads=THREADS)
+            # no record: the whole level is heavier than the bound held before it (>= d)
+            assert wmin >= w if w >= 0 else wmin > d, (j, r0)
+            if w >= 0 and r0 <= first < r1:
+                assert (wmin, rmin) == (w, first), (j, r0)
+    assert checked == 2
 
 
 def test_tensor_mid_level_stop(B):
