@@ -85,6 +85,9 @@ constexpr int kSchedWarp = 10;
 constexpr int kTcWarps = 11;
 constexpr int kTcThreads = kTcWarps * 32;
 constexpr int kTcMaxRegs = 168;
+static_assert((kTcWarps + 3) / 4 * 32 * kTcMaxRegs <= 16384, "register cap above a sub-partition's file");
+static_assert(kProdRows * 32 * kProdWarps == kTcM, "producer threads must cover the tile rows");
+static_assert(kSchedWarp == kTcWarps - 1 && kMmaWarp0 == kProdWarp0 + kProdWarps, "warp roles overlap");
 constexpr int kRing = 8;                   // work items between the scheduler and the others
 constexpr int kItemReaders = kEpiWarps + kProdWarps + kMmaWarps;   // warps that take each ring entry
 constexpr uint32_t kTmemCols = 512;
