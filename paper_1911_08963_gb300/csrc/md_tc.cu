@@ -437,6 +437,35 @@ __device__ __forceinline__ void xor_words(uint32_t (&S)[NW], const uint32_t *tab
         if (w0 + i < W) S[i] ^= tab[(w0 + i) * k + x];
 }
 
+// The epilogue's rare path, for a warp in which some row's maximum reached the threshold
+// (pass): those rows re-read their columns, take the first one holding the maximum (the
+// tail's smallest rank of that weight) and publish (weight, rank).  Out of line, so that the
+// epilogue's common path is compiled without it (inlined, it cost a quarter of the kernel's
+// throughput).  Returns the warp's best weight so far.
+template <int W>
+__device__ __noinline__ int tc_publish(const TcArgs a, uint32_t col0, int nchunk, int nvh, bool pass, float mx,
+                                       int p0, int ph, int s, unsigned long long tail, int ubest) {
+    int firstc = 0x7fffffff;
+    for (int c = 0; c < nchunk; c++) {
+        uint32_t vv[32];
+        tmem_ld32(col0 + 32u * c, vv);
+        tmem_wait(vv);
+#pragma unroll
+        for (int i = 0; i < 32; i++) {
+            const int col = 32 * c + i;
+            if (pass && col < nvh && col < firstc && __uint_as_float(vv[i]) == mx) firstc = col;
+        }
+    }
+    if (pass) {
+        const int w = a.base + (32 * W - (int)mx) / 2;
+        const unsigned long long rank = (unsigned long long)(p0 + firstc) + tail_rank_at(a, ph, s, tail);
+        atomicMin(&a.st->key[a.level], ((unsigned long long)w << kRankBits) | rank);
+        atomicMin(&a.st->U, (unsigned int)w);
+        ubest = min(ubest, w);
+    }
+    return ubest;
+}
+
 // ------------------------------------------------------------------------ kernel ----
 template <int W>
 __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
@@ -770,6 +799,9 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
             if (lane == 0) mbar_arrive(saddr(&sh.ifree[slot]));
             n++;
             if (it.end) break;
+            // the least accumulator value that improves on min(U, best): D >= K - 2 (min(U, best)
+            // - base); with a negative margin no row passes, since D <= K
+            float thrf = (float)(32 * W - 2 * (min(it.u, ubest) - a.base));
             for (int sl = 0; sl < it.nsl && ok; sl++) {
                 const int p0 = (it.sl0 + sl) * kTcN;
                 const int nvh = slice_heads(it, it.sl0 + sl);                                   // columns here
@@ -817,32 +849,18 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                     // tail index within the item: row r of tile t is tail R na (r mod 128 / R) +
                     // na (r div 128 / R) + t, R = kProdRows (na r + t with one row per thread)
                     const int row = kProdRows * it.na * (r % (kTcM / kProdRows)) + it.na * (r / (kTcM / kProdRows)) + t;
-                    const int thr = min(it.u, ubest) - a.base;
-                    const bool pass = row < it.nt && thr >= 0 && mx >= (float)(32 * W - 2 * thr);
-                    if (__any_sync(kFull, pass)) {
-                        // first column holding the row maximum = the tail's smallest rank of it
-                        int firstc = 0x7fffffff;
-                        for (int c = 0; c < nchunk; c++) {
-                            uint32_t vv[32];
-                            tmem_ld32(col0 + 32u * c, vv);
-                            tmem_wait(vv);
-#pragma unroll
-                            for (int i = 0; i < 32; i++) {
-                                const int col = 32 * c + i;
-                                if (pass && col < nvh && col < firstc && __uint_as_float(vv[i]) == mx) firstc = col;
-                            }
-                        }
-                        if (pass) {
-                            const int w = a.base + (32 * W - (int)mx) / 2;
-                            const unsigned long long rank = (unsigned long long)(p0 + firstc) +
-                                                            tail_rank_at(a, it.ph, it.s, it.t0 + (unsigned long long)row);
-                            atomicMin(&st->key[a.level], ((unsigned long long)w << kRankBits) | rank);
-                            atomicMin(&st->U, (unsigned int)w);
-                            ubest = min(ubest, w);
-                        }
-                    }
+                    const bool pass = mx >= thrf && row < it.nt;
                     tc_before();
-                    __syncwarp();
+                    // the vote also synchronises the warp before lane 0 releases the accumulator
+                    // (each lane's loads are complete at its wait)
+                    if (__any_sync(kFull, pass)) {
+                        tc_after();
+                        ubest = tc_publish<W>(a, col0, nchunk, nvh, pass, mx, p0, it.ph, it.s,
+                                              it.t0 + (unsigned long long)row, ubest);
+                        thrf = (float)(32 * W - 2 * (min(it.u, ubest) - a.base));
+                        tc_before();
+                        __syncwarp();
+                    }
                     if (lane == 0) mbar_arrive(saddr(&sh.tfree[acc]));
                     u++;
                 }
