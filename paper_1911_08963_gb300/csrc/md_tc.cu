@@ -45,7 +45,7 @@
 //     of a chain, while the epilogue drains whichever accumulator is done.
 //   * Four epilogue warps (one per tensor-memory lane quarter) read D with tcgen05.ld.red,
 //     which also returns each lane's maximum over the columns it loads, so no per-element
-//     arithmetic is left: two round trips of four loads per accumulator.  (Two warps of a
+//     arithmetic is left: two round trips of two 64-column loads per accumulator.  (Two warps of a
 //     sub-partition issuing tcgen05.ld.red while products run slowed the turnaround of the
 //     accumulators, hence one warp per quarter.)  A row reaching
 //     K - 2 (min(U, best) - base) is resolved to (weight, first rank) and published with
@@ -73,7 +73,7 @@ constexpr int kTcM = 128;                  // tails per tile (tensor-memory lane
 constexpr int kTcN = 256;                  // heads per slice (accumulator columns)
 // 11 warps: one SM sub-partition holds three of them, and its 16384 registers cap a thread at
 // 170, so 168 with the allocation unit of 8; a launch above the cap fails for lack of
-// registers, hence the explicit limit.  An epilogue warp keeps four 32-column loads (a
+// registers, hence the explicit limit.  An epilogue warp keeps two 64-column loads (a
 // 128-column half of an accumulator) in flight within it.
 constexpr int kEpiWarps = 4;               // warps 0-3: one per tensor-memory lane quarter
 constexpr int kProdWarp0 = 4;              // warps 4-7: one tile row per thread
@@ -304,6 +304,13 @@ __device__ __forceinline__ void tmem_wait_red2(float (&v)[32], float &rv, float 
 #undef MDL_R8
 #undef MDL_P8
 
+// 64 consecutive accumulator columns and their maximum (tcgen05.ld.red, sm_103a)
+__device__ __forceinline__ void tmem_ldmax64(uint32_t taddr, float (&v)[64], float &red) {
+    asm volatile("tcgen05.ld.red.sync.aligned.32x32b.x64.max.f32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, %64, [%65];" : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]), "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15]), "=f"(v[16]), "=f"(v[17]), "=f"(v[18]), "=f"(v[19]), "=f"(v[20]), "=f"(v[21]), "=f"(v[22]), "=f"(v[23]), "=f"(v[24]), "=f"(v[25]), "=f"(v[26]), "=f"(v[27]), "=f"(v[28]), "=f"(v[29]), "=f"(v[30]), "=f"(v[31]), "=f"(v[32]), "=f"(v[33]), "=f"(v[34]), "=f"(v[35]), "=f"(v[36]), "=f"(v[37]), "=f"(v[38]), "=f"(v[39]), "=f"(v[40]), "=f"(v[41]), "=f"(v[42]), "=f"(v[43]), "=f"(v[44]), "=f"(v[45]), "=f"(v[46]), "=f"(v[47]), "=f"(v[48]), "=f"(v[49]), "=f"(v[50]), "=f"(v[51]), "=f"(v[52]), "=f"(v[53]), "=f"(v[54]), "=f"(v[55]), "=f"(v[56]), "=f"(v[57]), "=f"(v[58]), "=f"(v[59]), "=f"(v[60]), "=f"(v[61]), "=f"(v[62]), "=f"(v[63]), "=f"(red) : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_red64(float (&v)[64], float &r) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]), "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]), "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]), "+f"(v[22]), "+f"(v[23]), "+f"(v[24]), "+f"(v[25]), "+f"(v[26]), "+f"(v[27]), "+f"(v[28]), "+f"(v[29]), "+f"(v[30]), "+f"(v[31]), "+f"(v[32]), "+f"(v[33]), "+f"(v[34]), "+f"(v[35]), "+f"(v[36]), "+f"(v[37]), "+f"(v[38]), "+f"(v[39]), "+f"(v[40]), "+f"(v[41]), "+f"(v[42]), "+f"(v[43]), "+f"(v[44]), "+f"(v[45]), "+f"(v[46]), "+f"(v[47]), "+f"(v[48]), "+f"(v[49]), "+f"(v[50]), "+f"(v[51]), "+f"(v[52]), "+f"(v[53]), "+f"(v[54]), "+f"(v[55]), "+f"(v[56]), "+f"(v[57]), "+f"(v[58]), "+f"(v[59]), "+f"(v[60]), "+f"(v[61]), "+f"(v[62]), "+f"(v[63]), "+f"(r)::"memory");
+}
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
     float r;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
@@ -661,17 +668,19 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                     for (int t = 0; t < cur.na; t++, u++) {
                         const int acc = (int)(u & 1);
                         if (acc != me) continue;
+                        // descriptors before the wait: the step of 32 K bytes (256 B of core
+                        // matrices) adds 256 >> 4 to the start-address field
+                        const uint64_t adesc = smem_desc(saddr(Atile + (set * T + t) * Cfg::kATile), 128u, Cfg::kSbo);
+                        const uint64_t bdesc = smem_desc(bbase, 128u, Cfg::kSbo);
+                        const uint32_t d = tmem + (uint32_t)(acc * kTcN);
                         if (u >= 2 && !mbar_wait(saddr(&sh.tfree[acc]), ((u >> 1) - 1) & 1, abort_flag)) {
                             ok = false;
                             break;
                         }
                         tc_after();
-                        const uint32_t abase = saddr(Atile + (set * T + t) * Cfg::kATile);
-                        const uint32_t d = tmem + (uint32_t)(acc * kTcN);
 #pragma unroll
                         for (int w = 0; w < W; w++)
-                            mma_e4m3(d, smem_desc(abase + 256u * w, 128u, Cfg::kSbo),
-                                     smem_desc(bbase + 256u * w, 128u, Cfg::kSbo), idesc, w > 0 ? 1u : 0u);
+                            mma_e4m3(d, adesc + (uint64_t)(16 * w), bdesc + (uint64_t)(16 * w), idesc, w > 0 ? 1u : 0u);
                         mma_commit(saddr(&sh.mdone[acc]));
                         last_acc = acc;
                         last_parity = (u >> 1) & 1;
@@ -813,17 +822,15 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                     const uint32_t col0 = lane_base + (uint32_t)(acc * kTcN);
                     float mx = -1e30f;
                     if (nvh == kTcN) {
-                        // all eight chunks whole: two round trips of four loads
+                        // all eight chunks whole: two round trips of two 64-column loads
 #pragma unroll 1
                         for (int h = 0; h < 2; h++) {
-                            float v0[32], v1[32], v2[32], v3[32], r0, r1, r2, r3;
-                            tmem_ldmax32(col0 + 128u * h, v0, r0);
-                            tmem_ldmax32(col0 + 128u * h + 32u, v1, r1);
-                            tmem_ldmax32(col0 + 128u * h + 64u, v2, r2);
-                            tmem_ldmax32(col0 + 128u * h + 96u, v3, r3);
-                            tmem_wait_red2(v0, r0, v1, r1);
-                            tmem_wait_red2(v2, r2, v3, r3);
-                            mx = fmax3(fmax3(r0, r1, r2), r3, mx);
+                            float v0[64], v1[64], r0, r1;
+                            tmem_ldmax64(col0 + 128u * h, v0, r0);
+                            tmem_ldmax64(col0 + 128u * h + 64u, v1, r1);
+                            tmem_wait_red64(v0, r0);
+                            tmem_wait_red64(v1, r1);
+                            mx = fmax3(r0, r1, mx);
                         }
                     } else
                     for (int c = 0; c < nchunk; c += 2) {
