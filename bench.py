@@ -37,7 +37,7 @@ NOMINAL_MAX_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch (level g=8 of rand200x100) measured
 # with ncu on the current kernels; to be re-measured when a kernel changes
 SPLIT_KERNEL_TRAFFIC_BYTES = 160256 + 700928
-TC_KERNEL_TRAFFIC_BYTES = 19200256
+TC_KERNEL_TRAFFIC_BYTES = 19184128
 FP8_PER_BF16 = 2.0                # nominal dense fp8 / bf16 tensor rate (4.5 / 2.25 PFLOP/s)
 
 
