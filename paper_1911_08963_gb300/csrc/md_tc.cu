@@ -45,16 +45,19 @@
 //     of a chain, while the epilogue drains whichever accumulator is done.
 //   * Four epilogue warps (one per tensor-memory lane quarter) read D with tcgen05.ld.red,
 //     which also returns each lane's maximum over the columns it loads, so no per-element
-//     arithmetic is left: two round trips of two 64-column loads per accumulator.  (Two warps of a
-//     sub-partition issuing tcgen05.ld.red while products run slowed the turnaround of the
-//     accumulators, hence one warp per quarter.)  A row reaching
-//     K - 2 (min(U, best) - base) is resolved to (weight, first rank) and published with
-//     atomicMin, as in the other level kernels.
+//     arithmetic is left: two round trips of two 64-column loads per accumulator.  (Two
+//     warps of a sub-partition issuing tcgen05.ld.red while products run slowed the
+//     turnaround of the accumulators, hence one warp per quarter.)  Per tile the common path
+//     is one compare with a threshold kept per item and one warp vote, which also orders the
+//     warp's loads before lane 0 frees the accumulator.  A row reaching
+//     K - 2 (min(U, best) - base) takes an out-of-line path: it is resolved to (weight, first
+//     rank) and published with atomicMin, as in the other level kernels.
 //   * One scheduler thread takes work items (s, head slices, run of tails) from the level's
 //     atomic counter, applies the mid-level stop, and passes them on through a ring in shared
 //     memory.
 // Every wait is bounded by the global timer; on expiry the block records MD_ETIMEOUT in the
-// state, waits (bounded) for its own tensor-core work, frees its tensor memory and returns.
+// state, stops the run, waits (bounded) for its own tensor-core work, frees its tensor memory
+// and returns.
 #include <cuda_runtime.h>
 
 #include <algorithm>
