@@ -142,6 +142,34 @@ def test_tensor_matches_split_kernel_stage10(B):
         assert sum(bin(int(x)).count("1") for x in row) == w
 
 
+@pytest.mark.parametrize("n,k,gmax,seed", [(256, 60, 8, 51), (256, 100, 7, 52), (230, 40, 9, 53), (240, 80, 7, 54)])
+def test_tensor_wide_rows_production_levels(B, n, k, gmax, seed):
+    """Wide packed rows at production level sizes (the default rule picks the tensor cores for
+    C(k, g) >= 2^28): W = 5..7, so tile sets of T = 2 and T = 1 tiles, up to five matrices
+    with a rank-deficient last one.  The records equal those of the popcount kernels and each
+    record's codeword (rows of Gamma_j at the record's colex rank) has the recorded weight."""
+    import math
+    G = T.pack(T.random_rows(n, k, seed), n)
+    _, _, _, lev_tc = run_gpu(B, G, n, k, max_stage=gmax, tensor=1)
+    _, _, _, lev_pc = run_gpu(B, G, n, k, max_stage=gmax, tensor=0)
+    assert lev_tc == lev_pc
+    assert any(math.comb(k, lv[0]) >= 1 << 28 for lv in lev_tc)
+    h = B.md_create(G, n, k, B.md_options_init())
+    try:
+        gam = {}
+        for g, j, w, first, _ in lev_tc:
+            if w < 0:
+                continue
+            if j not in gam:
+                gam[j] = B.md_gamma(h, j, n, k)[0]
+            row = np.zeros(gam[j].shape[1], dtype=np.uint64)
+            for c in O.colex_unrank(first, g, k):
+                row ^= gam[j][c]
+            assert sum(bin(int(x)).count("1") for x in row) == w, (g, j)
+    finally:
+        B.md_destroy(h)
+
+
 def test_tensor_stage10_record_is_window_minimum(B):
     """Sampled outputs at full size: for each level (10, j) the oracle scans colex-rank
     windows one combination at a time (the first ranks, ranks ending at the record, and
