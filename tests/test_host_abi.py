@@ -199,3 +199,32 @@ def test_level_plan_small_enumeration_exact(B):
                 got.append((T.colex_rank_formula(c), c))
     assert sorted(r for r, _ in got) == list(range(math.comb(k, g)))
     assert sorted(c for _, c in got) == list(itertools.combinations(range(k), g))
+
+
+def test_struct_layouts_match_header(B, tmp_path):
+    """The binding's ctypes mirrors have the sizes and field offsets of include/md.h (gcc
+    compiles a probe that prints them).  A drift would let the library write past a struct
+    that Python owns, as md_options_init does with the whole of md_options."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no gcc")
+    structs = [B.md_options, B.md_info, B.md_level, B.md_task_info, B.md_code, B.md_server_opts]
+    lines = ["#include <stdio.h>", "#include \"md.h\"", "int main(void) {"]
+    for S in structs:
+        name = S.__name__
+        lines.append('printf("%s size %%zu\\n", sizeof(%s));' % (name, name))
+        for f, _ in S._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (name, f, name, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    got = dict(line.rsplit(" ", 1) for line in out if line)
+    for S in structs:
+        assert int(got["%s size" % S.__name__]) == ctypes.sizeof(S), S.__name__
+        for f, _ in S._fields_:
+            assert int(got["%s.%s" % (S.__name__, f)]) == getattr(S, f).offset, (S.__name__, f)
