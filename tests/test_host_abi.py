@@ -228,3 +228,19 @@ def test_struct_layouts_match_header(B, tmp_path):
         assert int(got["%s size" % S.__name__]) == ctypes.sizeof(S), S.__name__
         for f, _ in S._fields_:
             assert int(got["%s.%s" % (S.__name__, f)]) == getattr(S, f).offset, (S.__name__, f)
+
+
+@pytest.mark.parametrize("n,k,g,tensor,why", [(200, 60, 15, 2, "v = 11 upper elements"),
+                                              (200, 100, 5, 1, "C(100, 5) < 2^28"),
+                                              (200, 100, 10, 0, "tensor = 0")])
+def test_level_plan_tensor_fallbacks(B, n, k, g, tensor, why):
+    """Levels the tensor-core kernel does not take keep the split plan: tails of more than
+    10 upper elements (g - q - 1 > 10), levels below 2^28 combinations under the default
+    rule, and tensor = 0."""
+    h = B.md_create(T.pack(T.random_rows(n, k, 6), n), n, k, B.md_options_init(tensor=tensor))
+    try:
+        kind, tasks, items = B.md_level_plan(h, g, 0)
+    finally:
+        B.md_destroy(h)
+    assert kind in (2, 3), why
+    assert tasks and items >= 1
