@@ -244,3 +244,32 @@ def test_level_plan_tensor_fallbacks(B, n, k, g, tensor, why):
         B.md_destroy(h)
     assert kind in (2, 3), why
     assert tasks and items >= 1
+
+
+@pytest.mark.parametrize("k,g,q,smin", [(12, 6, 3, 6), (13, 7, 2, 5), (11, 5, 3, 4), (10, 4, 3, 3), (12, 9, 3, 7)])
+def test_tensor_split_heads_are_colex_prefixes(k, g, q, smin):
+    """Brute force over all g-subsets, ranks from the oracle's colex rank: the heads the
+    tensor-core kernel pairs with a tail are a colex prefix of the head table (phase 0: the
+    q-subsets below s = c_{q+1} are the first C(s, q); phase 1: the (q+1)-subsets below
+    min(c_{q+2}, s_min) are the first C(min(c_{q+2}, s_min), q+1)), the rank splits into head
+    index + tail part, and the two phases meet every combination once."""
+    import itertools
+    import math
+    heads = {r: sorted(itertools.combinations(range(k), r), key=O.colex_rank) for r in (q, q + 1)}
+    seen = set()
+    for c in itertools.combinations(range(k), g):
+        if c[q] >= smin:                                   # phase 0: tail c_{q+1}..c_g
+            s, head, r = c[q], c[:q], q
+            allowed = math.comb(s, q)
+        else:                                              # phase 1: tail c_{q+2}..c_g
+            if g < q + 2:
+                continue
+            s, head, r = c[q + 1], c[:q + 1], q + 1
+            allowed = math.comb(min(s, smin), q + 1)
+        p = heads[r].index(head)
+        assert p < allowed
+        assert all(max(h) < min(s, smin) if r == q + 1 else max(h) < s for h in heads[r][:allowed])
+        tail = O.colex_rank(c) - O.colex_rank(head)
+        assert O.colex_rank(c) == p + tail
+        seen.add(c)
+    assert len(seen) == math.comb(k, g)                   # (s_min = q when g < q + 2, as planned)
