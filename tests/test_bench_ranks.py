@@ -43,3 +43,25 @@ def test_reduce_over_two_ranks():
 def test_reduce_single_process_is_identity():
     import bench
     assert bench.reduce_over_ranks(3.5, 7, "cpu") == (3.5, 7)
+
+
+def test_roofline_line_arithmetic():
+    """The tensor roofline: 2 x 32 W flops per codeword over the per-launch time, against
+    the sustained bf16 rate x 2 (fp8); the popcount roofline: one POPC per codeword against
+    16 x 152 x 2070 MHz."""
+    import types
+    import bench
+    peaks = bench.measured_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    args = types.SimpleNamespace(tensor=1)
+    r = bench.roofline_line(args, 200, 100, 10, 4, 1.7e13, 1.5)
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["achieved"] == pytest.approx(1.7e13 * 256 / 1.5 / 1e12)
+    assert r["peak"] == pytest.approx(2 * bf16)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["traffic"] == bench.TC_KERNEL_TRAFFIC_BYTES
+    args.tensor = 0
+    r = bench.roofline_line(args, 200, 100, 10, 4, 1.7e13, 5.0)
+    assert r["bound"] == "alu"
+    assert r["peak"] == pytest.approx(16 * 152 * 2070e6 / 1e9)
+    assert r["achieved"] == pytest.approx(1.7e13 / 5.0 / 1e9)
