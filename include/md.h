@@ -216,9 +216,10 @@ const char *md_strerror(int code);
  * md_scan_range_noalloc computes what md_scan_range computes -- the least weight over the
  * colex ranks [r0, r1) of the g-row combinations of a matrix, and the first rank reaching
  * it -- but makes no device allocation and no heap allocation of its own.  It is meant for
- * callers that cannot allocate: code that runs while a CUDA graph is being captured, real-time
- * loops that forbid allocation after start-up, and programs whose device memory belongs to
- * another allocator.
+ * callers that cannot allocate: real-time loops that forbid allocation after start-up (a
+ * cudaMalloc may wait for the whole device and take an unbounded time), and programs whose
+ * device memory belongs to another allocator (a framework's caching pool that already holds
+ * the free memory, or a fixed budget that an outside allocation would break).
  * The paper has no counterpart to this entry point.
  *
  *   rows         device pointer, 16-byte aligned, owned by the caller: k packed rows of
@@ -237,7 +238,8 @@ const char *md_strerror(int code);
  * stream capture).  Every call resets the scratch before use, and all calls share it: calls
  * that overlap on the GPU (from several threads or streams) race and give wrong results.
  * k > MD_NOALLOC_MAX_K, or more than 2^55 combinations, returns MD_EUNSUPPORTED; a bad
- * pointer alignment or argument returns MD_EINVAL. */
+ * pointer alignment or argument returns MD_EINVAL; a failed CUDA call (including the device
+ * queries of the first call) returns MD_ECUDA. */
 #define MD_NOALLOC_MAX_K 128
 #define MD_NOALLOC_SCRATCH_BYTES 139264
 int md_scan_range_noalloc(const uint32_t *rows, int k, int words, int weight_base, int g, uint64_t r0,

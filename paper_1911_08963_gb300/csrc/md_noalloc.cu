@@ -1,10 +1,10 @@
 // md_noalloc.cu -- md_scan_range_noalloc: the rank-range scan for callers that must not
 // allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being captured,
-// real-time or embedded loops that forbid allocation after start-up, and processes whose
-// device memory is owned by another allocator (a framework's caching allocator) that this
-// library must not bypass.  This entry point gives them the colex rank-range scan with no
+// Some callers cannot call cudaMalloc: real-time or embedded loops that forbid allocation
+// after start-up (an allocation may wait for the whole device), and processes whose device
+// memory is owned by another allocator (a framework's caching allocator) that this library
+// must not bypass.  This entry point gives them the colex rank-range scan with no
 // allocation: its device scratch (the bound U, the work-item counter, the result key and a
 // binomial table) lives in one file-scope __device__ array of fixed size that every GPU
 // loading the library holds until the process exits.
@@ -129,8 +129,11 @@ extern "C" int md_scan_range_noalloc(const uint32_t *rows, int k, int words, int
     cudaStream_t s = (cudaStream_t)stream;
     const uint64_t span = r1 - r0;
     int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+        cudaGetLastError();
+        return MD_ECUDA;
+    }
     unsigned long long per_chunk = span / (32ull * (unsigned long long)sms * 16);
     if (per_chunk < 1) per_chunk = 1;
     if (per_chunk > 4096) per_chunk = 4096;

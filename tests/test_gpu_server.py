@@ -1,14 +1,19 @@
-"""GPU: the continuous-batching server returns, for every request, exactly what md_compute
-returns for that code alone, while requests join and leave the running mix."""
+"""GPU: the continuous-batching server returns, for every request, exactly what the CPU
+oracle returns for that code (d and the canonical witness), and what md_compute returns for it
+alone, while requests join and leave the running mix."""
+import os
 import time
 
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1911_08963_gb300 import inputs as I
 from tests import textbook as T
 
 pytestmark = pytest.mark.gpu
+
+THREADS = os.cpu_count() or 4
 
 
 @pytest.fixture(scope="module")
@@ -25,6 +30,11 @@ def single(B, G, n, k):
         return B.md_compute(h, n)
     finally:
         B.md_destroy(h)
+
+
+def assert_oracle(G, n, k, d, wit):
+    ref = O.bz(G, n, k, threads=THREADS)
+    assert d == ref.d and np.array_equal(wit, ref.witness), (n, k, d, ref.d)
 
 
 def wait(B, s, ticket, n, timeout=120):
@@ -48,6 +58,7 @@ def test_server_results_equal_alone(B):
         out = [wait(B, s, t, n) for t, (G, n, k) in zip(tickets, codes)]
         for (G, n, k), (d, wit, st) in zip(codes, out):
             assert st == B.MD_OK
+            assert_oracle(G, n, k, d, wit)
             ds, ws = single(B, G, n, k)
             assert d == ds and np.array_equal(wit, ws)
         # a ticket is returned once
@@ -59,7 +70,8 @@ def test_server_results_equal_alone(B):
 
 def test_server_overlap_small_finishes_before_large(B):
     """A small code submitted while a large one (~2e12 combinations) runs is admitted into the
-    running mix and finishes first; both results equal md_compute's."""
+    running mix and finishes first; the small result equals the oracle's, and both equal
+    md_compute's (the large one is beyond the oracle in test time)."""
     s = B.md_server_create(slots=4)
     try:
         n, k = 176, 88
@@ -71,6 +83,8 @@ def test_server_overlap_small_finishes_before_large(B):
         d_small = wait(B, s, ts, 40)
         assert B.md_server_poll(s, tl, n) is None          # the large code is still running
         d_large = wait(B, s, tl, n)
+        assert d_small[2] == B.MD_OK and d_large[2] == B.MD_OK
+        assert_oracle(*small, d_small[0], d_small[1])
         assert d_small[0] == single(B, *small)[0]
         ds, ws = single(B, G, n, k)
         assert d_large[0] == ds and np.array_equal(d_large[1], ws)
@@ -96,8 +110,10 @@ def test_server_rejections(B):
 
 
 def test_server_trace_sample(B):
-    """First requests of the Poisson trace with a work budget: accepted ones equal md_compute."""
-    s = B.md_server_create(slots=16, work_budget=2 * 10 ** 10)
+    """First requests of the Poisson trace with a work budget (requests whose estimated work
+    exceeds it are refused at submission): every accepted one equals the oracle and
+    md_compute."""
+    s = B.md_server_create(slots=16, work_budget=3 * 10 ** 9)
     try:
         trace = I.serving_trace(40)
         tickets = []
@@ -107,9 +123,10 @@ def test_server_trace_sample(B):
             except B.MDError as e:
                 assert e.code == B.MD_EBUDGET
         assert tickets
-        for tk, G, n, k in tickets:
-            d, wit, st = wait(B, s, tk, n)
+        outs = [wait(B, s, tk, n) for tk, G, n, k in tickets]
+        for (tk, G, n, k), (d, wit, st) in zip(tickets, outs):
             assert st == B.MD_OK
+            assert_oracle(G, n, k, d, wit)
             ds, ws = single(B, G, n, k)
             assert d == ds and np.array_equal(wit, ws)
     finally:

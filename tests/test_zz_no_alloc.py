@@ -1,20 +1,26 @@
 """md_scan_range_noalloc: the rank-range scan for callers that cannot allocate device memory.
 
-Such callers (code running under CUDA graph capture, real-time loops that forbid allocation,
-programs whose device memory belongs to another allocator) pass their own device copy of the
-packed rows; the entry point keeps its scratch in a fixed array inside the library.  This test
-checks, through the C ABI, that two calls in a row give exactly what md_scan_range gives (the
-results are integers: tolerance zero).  It sits in a file of its own that is collected last.
+Such callers (real-time loops that forbid allocation after start-up, programs whose device
+memory belongs to another allocator) pass their own device copy of the packed rows; the entry
+point keeps its scratch in a fixed array inside the library.  This test checks, through the C
+ABI, that consecutive calls give exactly what the CPU oracle's scan of the same colex ranks
+gives, and what md_scan_range gives (the results are integers: tolerance zero).  It sits in a
+file of its own that is collected last.
 """
+import os
+
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1911_08963_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
+THREADS = os.cpu_count() or 4
 
-def test_noalloc_scan_equals_scan_range_twice():
+
+def test_noalloc_scan_equals_oracle_and_scan_range_twice():
     torch = pytest.importorskip("torch")
     from paper_1911_08963_gb300 import build
     build.build()
@@ -29,11 +35,21 @@ def test_noalloc_scan_equals_scan_range_twice():
         assert rows32.shape == (k, 8)
         dev = torch.from_numpy(rows32.copy()).cuda()
         torch.cuda.synchronize()
-        cases = [(7, 10 ** 9, 10 ** 9 + 3 * 10 ** 6, -1), (4, 0, 3921225, -1), (7, 10 ** 9, 10 ** 9 + 3 * 10 ** 6, 40)]
+        gams, _, _ = O.gammas(G, n, k)
+        assert np.array_equal(gams[1], gam)
+        cases = [(7, 10 ** 9, 10 ** 9 + 3 * 10 ** 6, -1), (4, 0, 3921225, -1),
+                 (7, 10 ** 9, 10 ** 9 + 3 * 10 ** 6, 40), (7, 10 ** 9, 10 ** 9 + 3 * 10 ** 6, 60),
+                 (3, 5, 5, -1)]
         for g, r0, r1, bound in cases:          # consecutive calls share the scratch array
             got = B.md_scan_range_noalloc(dev.data_ptr(), k, 7, 0, g, r0, r1, bound)
             want = B.md_scan_range(h, g, 1, r0, r1, bound)
             assert got == want, (g, r0, r1, bound, got, want)
+            if r1 > r0:
+                w, first = O.scan(gams[1], n, k, g, r0, r1, threads=THREADS)
+                ref = (w, first) if bound < 0 or w <= bound else (-1, 0)
+            else:
+                ref = (-1, 0)
+            assert got == ref, (g, r0, r1, bound, got, ref)
         with pytest.raises(B.MDError) as e:
             B.md_scan_range_noalloc(dev.data_ptr(), 129, 7, 0, 3, 0, 10)
         assert e.value.code == B.MD_EUNSUPPORTED
