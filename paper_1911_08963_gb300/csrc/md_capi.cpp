@@ -409,7 +409,7 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
                 a = level_args(h, p, level, false);
                 err |= launch_tc_level(h->dev.heads[p.j], h->dev.heads2[p.j], p.tc_smin, h->dev.rows[p.j],
                                        h->dev.binom, h->dev.st, k, p.g, p.tc_q, p.base, level, c.gam[p.j].W,
-                                       c.gam[p.j].WP, 1, h->sms, h->opt.test_stall, s) != 0;
+                                       c.gam[p.j].WP, 1, h->sms, h->opt.test_stall, p.tc_words8, s) != 0;
             } else {
                 LaunchCfg L = launch_cfg(h, p);
                 a = level_args(h, p, level, L.h2s);

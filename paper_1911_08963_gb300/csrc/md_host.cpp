@@ -305,7 +305,7 @@ double estimate_work(const Code &c, int *d_est, int *g_stop) {
     return work;
 }
 
-int filter_threshold(const Gamma &gm, int f) {
+int filter_threshold(const Gamma &gm, int f, double pmax) {
     const int bits = (int)gm.packed_cols.size();
     // per bit position b of a 32-bit word: how many of the first f words have a column there
     double dist[33] = {1.0};
@@ -321,7 +321,7 @@ int filter_threshold(const Gamma &gm, int f) {
     int best = -1;
     for (int t = 0; t <= 32; t++) {
         cdf += dist[t];
-        if (cdf < 1e-5) best = t; else break;
+        if (cdf < pmax) best = t; else break;
     }
     return best;
 }
@@ -333,9 +333,26 @@ unsigned long long filter_thresholds(const Gamma &gm, int mode) {
     unsigned long long out = 0;
     if (mode == 0) return 0;
     for (int f = 1; f <= gm.W && f <= 8; f++) {
-        int t = filter_threshold(gm, f);
+        int t = filter_threshold(gm, f, 1e-5);
         if (mode == 2 && f == gm.W) t = 254;
         if (mode == 3) t = (f == 1) ? 254 : -1;
+        const unsigned long long byte = (unsigned long long)(t < 0 ? 0 : std::min(255, t + 1));
+        out |= byte << (8 * (f - 1));
+    }
+    return out;
+}
+
+// Word counts of the tensor-core product.  A product over the first f packed words gives the
+// weight of those words only, a lower bound of the weight; byte f-1 holds 1 + the largest
+// packed-weight threshold at which that bound rejects all but a fraction 1e-7 of random
+// codewords (0 = never), and the last word count, the exact product, is always usable (255).
+// mode 0: always every word; 3: always one word (a test setting: most products then send
+// rows to the exact check); otherwise adaptive.
+unsigned long long tc_word_thresholds(const Gamma &gm, int mode) {
+    unsigned long long out = 0;
+    for (int f = 1; f <= gm.W && f <= 8; f++) {
+        int t = f == gm.W ? 254 : (mode == 0 ? -1 : filter_threshold(gm, f, 1e-7));
+        if (mode == 3) t = f == 1 ? 254 : -1;
         const unsigned long long byte = (unsigned long long)(t < 0 ? 0 : std::min(255, t + 1));
         out |= byte << (8 * (f - 1));
     }
@@ -373,6 +390,7 @@ LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o) {
             p.v = v;
             p.tc_smin = g >= q + 2 ? tc_split_point(k, q) : q;
             p.nchunks = tc_level_items(k, g, q, p.tc_smin, gm.W);
+            p.tc_words8 = tc_word_thresholds(gm, o.filter);
             return p;
         }
     }

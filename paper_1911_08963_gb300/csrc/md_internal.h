@@ -98,6 +98,7 @@ struct LevelPlan {
     std::vector<MEntry> mtab;       // kinds 2, 3
     int tc_q = 0;                   // kind 4: head size q (tail = the other g - q elements)
     int tc_smin = 0;                // kind 4: combinations with c_{q+1} < tc_smin use (q+1)-heads
+    unsigned long long tc_words8 = 0;   // kind 4: word counts of the product (tc_word_thresholds)
 };
 
 struct PlanOptions {
@@ -123,8 +124,9 @@ LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o);
 
 // Largest threshold t with P(popcount(OR of the first f packed words) <= t) below 1e-5 for
 // uniformly random packed rows (-1 if none): above it the filter would rarely reject.
-int filter_threshold(const Gamma &gm, int f);
+int filter_threshold(const Gamma &gm, int f, double pmax);
 unsigned long long filter_thresholds(const Gamma &gm, int mode);
+unsigned long long tc_word_thresholds(const Gamma &gm, int mode);
 
 // -------------------------------------------------------------------- device side ---
 
@@ -225,9 +227,10 @@ int launch_h2_build(const uint32_t *rows, uint32_t *h2, int k, int WP, void *str
 int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, int k, int q, int W, int WP,
                      uint64_t nheads, unsigned char *tables, void *stream);
 // One tensor-core level: `blocks` persistent blocks (one per SM), work items from st->ctr[level].
+// words8: the product's word counts per threshold (LevelPlan::tc_words8).
 int launch_tc_level(const unsigned char *tables, const unsigned char *tables2, int smin, const uint32_t *rows,
                     const unsigned long long *binom_d, DevState *st, int k, int g, int q, int base, int level, int W,
-                    int WP, int check_stop, int blocks, int stall, void *stream);
+                    int WP, int check_stop, int blocks, int stall, unsigned long long words8, void *stream);
 int launch_level(const LevelArgs &a, int kind, int W, int WP, int blocks, int threads, size_t smem,
                  void *stream);
 int launch_finalize(const LevelArgs &a, void *stream);

@@ -121,6 +121,7 @@ struct TcItem {
     int u;                                 // U when the item was handed out
     int end;                               // 1: the level has no more items
     int ph;                                // phase: heads of q + ph elements
+    int F;                                 // packed words in the product (1..W): see TcArgs::words8
 };
 
 // Heads of slice sl that belong to s (the MMA N covers them rounded up to 16).
@@ -362,6 +363,11 @@ struct TcArgs {
     int bsub;                              // 1: C(x, i), i <= kMaxV, staged in shared memory
     int smin;                              // phase split (q: no second phase)
     int stall;                             // test hook: the first tile set is never signalled
+    // Products over the first F packed words only give the weight of those words, a lower bound
+    // of the codeword's weight: byte f-1 = 1 + the largest packed-weight threshold U - base at
+    // which f words still reject all but a tiny fraction of codewords (0 = never; the byte of
+    // f = W, the exact product, is 255).  An item takes the fewest qualifying words.
+    unsigned long long words8;
 };
 
 __device__ __forceinline__ unsigned long long C(const TcArgs &a, int n, int r) {
@@ -448,30 +454,90 @@ __device__ __forceinline__ void xor_words(uint32_t (&S)[NW], const uint32_t *tab
 }
 
 // The epilogue's rare path, for a warp in which some row's maximum reached the threshold
-// (pass): those rows re-read their columns, take the first one holding the maximum (the
-// tail's smallest rank of that weight) and publish (weight, rank).  Out of line, so that the
-// epilogue's common path is compiled without it (inlined, it cost a quarter of the kernel's
-// throughput).  Returns the warp's best weight so far.
+// (pass).  Out of line, so that the epilogue's common path is compiled without it (inlined,
+// it cost a quarter of the kernel's throughput).  Returns the warp's best weight so far.
+//   * F = W: the product is the exact weight.  The passing rows re-read their columns, take
+//     the first one holding the maximum (the tail's smallest rank of that weight) and publish
+//     (weight, rank).
+//   * F < W: the product covered the first F packed words only, so D >= thrf marks codewords
+//     whose weight over those words -- a lower bound of the weight -- can still reach
+//     T = min(U, best).  Each such column's exact weight is counted from the rows: the tail
+//     sum (its elements by unranking) XOR the head sum (the head's q + ph elements by colex
+//     unranking of its index), over all W words.  The lightest one, first in column order,
+//     is published if it reaches T.
 template <int W>
-__device__ __noinline__ int tc_publish(const TcArgs a, uint32_t col0, int nchunk, int nvh, bool pass, float mx,
-                                       int p0, int ph, int s, unsigned long long tail, int ubest) {
-    int firstc = 0x7fffffff;
-    for (int c = 0; c < nchunk; c++) {
-        uint32_t vv[32];
-        tmem_ld32(col0 + 32u * c, vv);
-        tmem_wait(vv);
+__device__ __noinline__ int tc_publish(const TcArgs a, const uint32_t *rT, const unsigned long long *bs, uint32_t col0,
+                                       int nchunk, int nvh, bool pass, float mx, float thrf, int F, int p0, int ph,
+                                       int s, unsigned long long tail, int ubest, int u) {
+    const int k = a.k;
+    if (F == W) {
+        int firstc = 0x7fffffff;
+        for (int c = 0; c < nchunk; c++) {
+            uint32_t vv[32];
+            __syncwarp();
+            tmem_ld32(col0 + 32u * c, vv);
+            tmem_wait(vv);
 #pragma unroll
-        for (int i = 0; i < 32; i++) {
-            const int col = 32 * c + i;
-            if (pass && col < nvh && col < firstc && __uint_as_float(vv[i]) == mx) firstc = col;
+            for (int i = 0; i < 32; i++) {
+                const int col = 32 * c + i;
+                if (pass && col < nvh && col < firstc && __uint_as_float(vv[i]) == mx) firstc = col;
+            }
+        }
+        if (pass) {
+            const int w = a.base + (32 * W - (int)mx) / 2;
+            const unsigned long long rank = (unsigned long long)(p0 + firstc) + tail_rank_at(a, ph, s, tail);
+            atomicMin(&a.st->key[a.level], ((unsigned long long)w << kRankBits) | rank);
+            atomicMin(&a.st->U, (unsigned int)w);
+            ubest = min(ubest, w);
+        }
+        return ubest;
+    }
+    const int qq = a.q + ph, v = a.g - qq - 1;
+    uint32_t S[W];
+#pragma unroll
+    for (int w = 0; w < W; w++) S[w] = 0u;
+    if (pass) {
+        int o[kMaxV];
+        tail_unrank(a, bs, s, v, tail, o);
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            S[w] = rT[w * k + s];
+            for (int i = 0; i < v; i++) S[w] ^= rT[w * k + o[i]];
         }
     }
-    if (pass) {
-        const int w = a.base + (32 * W - (int)mx) / 2;
-        const unsigned long long rank = (unsigned long long)(p0 + firstc) + tail_rank_at(a, ph, s, tail);
-        atomicMin(&a.st->key[a.level], ((unsigned long long)w << kRankBits) | rank);
-        atomicMin(&a.st->U, (unsigned int)w);
-        ubest = min(ubest, w);
+    int bw = 0x7fffffff, bc = -1;
+    for (int c = 0; c < nchunk; c++) {
+        uint32_t vv[32];
+        __syncwarp();
+        tmem_ld32(col0 + 32u * c, vv);
+        tmem_wait(vv);
+        if (!pass) continue;
+        for (int i = 0; i < 32; i++) {
+            const int col = 32 * c + i;
+            if (col >= nvh || __uint_as_float(vv[i]) < thrf) continue;
+            uint32_t H[W];
+#pragma unroll
+            for (int w = 0; w < W; w++) H[w] = S[w];
+            unsigned long long t = (unsigned long long)(p0 + col);
+            int hi = s - 1;                                  // the heads of s lie below s
+            for (int e = qq; e >= 1; e--) {
+                const int x = colex_digit(a, e - 1, hi, e, t);
+                t -= C(a, x, e);
+                hi = x - 1;
+#pragma unroll
+                for (int w = 0; w < W; w++) H[w] ^= rT[w * k + x];
+            }
+            int wt = a.base;
+#pragma unroll
+            for (int w = 0; w < W; w++) wt += __popc(H[w]);
+            if (wt < bw) { bw = wt; bc = col; }
+        }
+    }
+    if (pass && bc >= 0 && bw <= min(u, ubest)) {
+        const unsigned long long rank = (unsigned long long)(p0 + bc) + tail_rank_at(a, ph, s, tail);
+        atomicMin(&a.st->key[a.level], ((unsigned long long)bw << kRankBits) | rank);
+        atomicMin(&a.st->U, (unsigned int)bw);
+        ubest = min(ubest, bw);
     }
     return ubest;
 }
@@ -590,6 +656,9 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                     it.na = (it.nt + kTcM - 1) / kTcM;
                     const int U = (int)*(volatile unsigned int *)&st->U;
                     it.u = U;
+                    it.F = W;
+                    for (int f = 1; f < W; f++)
+                        if ((int)((a.words8 >> (8 * (f - 1))) & 255ull) > U - a.base) { it.F = f; break; }
                     // mid-level stop: once U <= L this level holds the answer's weight, and an
                     // item whose smallest rank lies above the best rank of that weight can go
                     if (a.check_stop && U <= *(volatile int *)&st->L) {
@@ -683,7 +752,8 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                         tc_after();
 #pragma unroll
                         for (int w = 0; w < W; w++)
-                            mma_e4m3(d, adesc + (uint64_t)(16 * w), bdesc + (uint64_t)(16 * w), idesc, w > 0 ? 1u : 0u);
+                            if (w < cur.F)
+                                mma_e4m3(d, adesc + (uint64_t)(16 * w), bdesc + (uint64_t)(16 * w), idesc, w > 0 ? 1u : 0u);
                         mma_commit(saddr(&sh.mdone[acc]));
                         last_acc = acc;
                         last_parity = (u >> 1) & 1;
@@ -756,6 +826,7 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                     const bool valid = m < cnt;
 #pragma unroll
                     for (int i = 0; i < NW; i++) {
+                        if (i >= it.F) continue;               // the item's products read F words
                         uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
                         if (valid) sign_word(Sx[i], 0x38383838u, lo, hi);
                         *reinterpret_cast<uint4 *>(rowp + i * 256) = lo;
@@ -811,9 +882,10 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
             if (lane == 0) mbar_arrive(saddr(&sh.ifree[slot]));
             n++;
             if (it.end) break;
-            // the least accumulator value that improves on min(U, best): D >= K - 2 (min(U, best)
-            // - base); with a negative margin no row passes, since D <= K
-            float thrf = (float)(32 * W - 2 * (min(it.u, ubest) - a.base));
+            // the least accumulator value that can reach min(U, best): D >= K - 2 (min(U, best) -
+            // base) with K = 32 F the product's bits (its weight is that of the first F words, a
+            // lower bound when F < W); with a negative margin no row passes, since D <= K
+            float thrf = (float)(32 * it.F - 2 * (min(it.u, ubest) - a.base));
             for (int sl = 0; sl < it.nsl && ok; sl++) {
                 const int p0 = (it.sl0 + sl) * kTcN;
                 const int nvh = slice_heads(it, it.sl0 + sl);                                   // columns here
@@ -865,9 +937,9 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                     // (each lane's loads are complete at its wait)
                     if (__any_sync(kFull, pass)) {
                         tc_after();
-                        ubest = tc_publish<W>(a, col0, nchunk, nvh, pass, mx, p0, it.ph, it.s,
-                                              it.t0 + (unsigned long long)row, ubest);
-                        thrf = (float)(32 * W - 2 * (min(it.u, ubest) - a.base));
+                        ubest = tc_publish<W>(a, rT, bsub, col0, nchunk, nvh, pass, mx, thrf, it.F, p0, it.ph,
+                                              it.s, it.t0 + (unsigned long long)row, ubest, it.u);
+                        thrf = (float)(32 * it.F - 2 * (min(it.u, ubest) - a.base));
                         tc_before();
                         __syncwarp();
                     }
@@ -1007,14 +1079,14 @@ int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, in
 
 int launch_tc_level(const unsigned char *tables, const unsigned char *tables2, int smin, const uint32_t *rows,
                     const unsigned long long *binom_d, DevState *st, int k, int g, int q, int base, int level, int W,
-                    int WP, int check_stop, int blocks, int stall, void *stream) {
+                    int WP, int check_stop, int blocks, int stall, unsigned long long words8, void *stream) {
     int dev = 0, optin = 0, with_bsub = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return (int)cudaErrorInvalidValue;
     const size_t smem = (size_t)tc_smem_bytes(k, W, optin, &with_bsub);
     TcArgs a{{tables, tables2}, rows, binom_d, st, k, g, q, base, level, WP, tc_tiles_per_set(W), check_stop,
-             with_bsub, smin, stall};
+             with_bsub, smin, stall, words8};
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     switch (W) {

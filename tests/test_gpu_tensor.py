@@ -80,6 +80,18 @@ def test_forced_tensor_levels(B, n, k, seed, q):
     assert_parity(B, G, n, k, res, tensor=2, tensor_head=q)
 
 
+@pytest.mark.parametrize("n,k,seed", CASES)
+@pytest.mark.parametrize("filt", [0, 3])
+def test_forced_tensor_product_words(B, n, k, seed, filt):
+    """The product's word count: filter = 0 always multiplies every packed word (the product is
+    the exact weight); filter = 3 always multiplies the first word only, so the product is a
+    lower bound and nearly every row goes through the exact recheck of its candidate columns
+    (tail sum XOR head sum over all words).  Both must give exactly the oracle's results."""
+    G = T.pack(T.random_rows(n, k, seed), n)
+    res = oracle_cached(G, n, k, (n, k, seed))
+    assert_parity(B, G, n, k, res, tensor=2, tensor_head=3, filter=filt)
+
+
 @pytest.mark.parametrize("n,k,seed", [(90, 30, 33), (100, 33, 41), (120, 40, 34)])
 def test_forced_tensor_per_matrix_rule(B, n, k, seed):
     G = T.pack(T.random_rows(n, k, seed), n)
