@@ -141,7 +141,10 @@ typedef struct md_info {
 typedef struct md_level {
     int g, j;
     int weight;
-    int pad;
+    int words;                     /* tensor-core levels: packed 32-bit words in each product at
+                                      the level's start (a bound over fewer words than the row
+                                      holds filters codewords, see md_options.filter); 0 for
+                                      the popcount kernels */
     uint64_t first_rank;
     uint64_t count;                /* C(k, g) */
     double seconds;                /* device time of the level's enumeration kernel */

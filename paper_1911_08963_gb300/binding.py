@@ -45,7 +45,7 @@ class md_info(ctypes.Structure):
 
 
 class md_level(ctypes.Structure):
-    _fields_ = [("g", ctypes.c_int), ("j", ctypes.c_int), ("weight", ctypes.c_int), ("pad", ctypes.c_int),
+    _fields_ = [("g", ctypes.c_int), ("j", ctypes.c_int), ("weight", ctypes.c_int), ("words", ctypes.c_int),
                 ("first_rank", ctypes.c_uint64), ("count", ctypes.c_uint64), ("seconds", ctypes.c_double)]
 
 
@@ -158,12 +158,12 @@ def md_info_get(h: int) -> dict:
 
 
 def md_levels(h: int, with_time: bool = False):
-    """[(g, j, weight, first_rank, count)] (+ kernel seconds if with_time)."""
+    """[(g, j, weight, first_rank, count)] (+ kernel seconds and product words if with_time)."""
     buf = (md_level * MD_MAX_LEVELS)()
     cnt = ctypes.c_int()
     _check(lib.md_levels(h, buf, MD_MAX_LEVELS, ctypes.byref(cnt)), "md_levels")
     if with_time:
-        return [(r.g, r.j, r.weight, r.first_rank, r.count, r.seconds) for r in buf[:cnt.value]]
+        return [(r.g, r.j, r.weight, r.first_rank, r.count, r.seconds, r.words) for r in buf[:cnt.value]]
     return [(r.g, r.j, r.weight, r.first_rank, r.count) for r in buf[:cnt.value]]
 
 

@@ -468,6 +468,13 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
             r.first_rank = key & (kRankLimit - 1);
         }
         r.seconds = lv < (int)lev_sec.size() ? lev_sec[lv] : 0.0;
+        if (p.kind == KIND_TC) {
+            // the scheduler's word count for the U the level started with (U only drops later)
+            const int W = c.gam[p.j].W, thr = (int)st.u_in[lv] - p.base;
+            r.words = W;
+            for (int f = 1; f < W; f++)
+                if ((int)((p.tc_words8 >> (8 * (f - 1))) & 255ull) > thr) { r.words = f; break; }
+        }
         if (key_level < 0 && r.weight == U) key_level = lv;
         evaluated += p.count;
         h->levels.push_back(r);

@@ -348,10 +348,13 @@ unsigned long long filter_thresholds(const Gamma &gm, int mode) {
 // codewords (0 = never), and the last word count, the exact product, is always usable (255).
 // mode 0: always every word; 3: always one word (a test setting: most products then send
 // rows to the exact check); otherwise adaptive.
+#ifndef MD_TC_WORD_PMAX
+#define MD_TC_WORD_PMAX 1e-7
+#endif
 unsigned long long tc_word_thresholds(const Gamma &gm, int mode) {
     unsigned long long out = 0;
     for (int f = 1; f <= gm.W && f <= 8; f++) {
-        int t = f == gm.W ? 254 : (mode == 0 ? -1 : filter_threshold(gm, f, 1e-7));
+        int t = f == gm.W ? 254 : (mode == 0 ? -1 : filter_threshold(gm, f, MD_TC_WORD_PMAX));
         if (mode == 3) t = f == 1 ? 254 : -1;
         const unsigned long long byte = (unsigned long long)(t < 0 ? 0 : std::min(255, t + 1));
         out |= byte << (8 * (f - 1));

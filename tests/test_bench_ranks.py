@@ -46,22 +46,29 @@ def test_reduce_single_process_is_identity():
 
 
 def test_roofline_line_arithmetic():
-    """The tensor roofline: 2 x 32 W flops per codeword over the per-launch time, against
-    the sustained bf16 rate x 2 (fp8); the popcount roofline: one POPC per codeword against
-    16 x 152 x 2070 MHz."""
+    """The tensor roofline: 2 x 32 F flops per codeword (F = the product's packed words) over
+    the per-launch time, against the sustained bf16 rate x 2 (fp8), with the method's own work
+    (2 (n - k) flops per codeword) beside it; the popcount roofline: one POPC per codeword
+    against 16 x 152 x 2070 MHz."""
     import types
     import bench
     peaks = bench.measured_peaks()
     bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
     args = types.SimpleNamespace(tensor=1)
-    r = bench.roofline_line(args, 200, 100, 10, 4, 1.7e13, 1.5)
+    r = bench.roofline_line(args, 200, 100, 10, 4, 1.7e13, 1.5, 3)
     assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
-    assert r["achieved"] == pytest.approx(1.7e13 * 256 / 1.5 / 1e12)
+    assert r["achieved"] == pytest.approx(1.7e13 * 192 / 1.5 / 1e12)
     assert r["peak"] == pytest.approx(2 * bf16)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["method"]["achieved"] == pytest.approx(1.7e13 * 200 / 1.5 / 1e12)
+    assert r["method"]["frac"] == pytest.approx(r["method"]["achieved"] / r["peak"])
+    assert r["peak_codewords_per_s"] == pytest.approx(2 * bf16 * 1e12 / 192)
     assert r["traffic"] == bench.TC_KERNEL_TRAFFIC_BYTES
+    # no word count reported: the full packed width (W = 4 for n - k = 100)
+    r = bench.roofline_line(args, 200, 100, 10, 4, 1.7e13, 1.5, 0)
+    assert r["achieved"] == pytest.approx(1.7e13 * 256 / 1.5 / 1e12)
     args.tensor = 0
-    r = bench.roofline_line(args, 200, 100, 10, 4, 1.7e13, 5.0)
+    r = bench.roofline_line(args, 200, 100, 10, 4, 1.7e13, 5.0, 0)
     assert r["bound"] == "alu"
     assert r["peak"] == pytest.approx(16 * 152 * 2070e6 / 1e9)
     assert r["achieved"] == pytest.approx(1.7e13 / 5.0 / 1e9)
