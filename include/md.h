@@ -77,8 +77,12 @@ typedef struct md_options {
                                  when no word count qualifies; 3 = always filter with one
                                  word (a test setting).  Results are identical for all. */
     void *stream;             /* cudaStream_t to run on; NULL = the library's own stream */
-    volatile int *cancel_flag;/* optional host flag (pinned or ordinary memory): set non-zero
-                                 to cancel; polled between stages */
+    volatile int *cancel_flag;/* optional host flag (ordinary or pinned memory): set non-zero,
+                                 from any thread, to cancel a running md_compute, which then
+                                 returns MD_ECANCELED.  While the device works the calling
+                                 thread polls it (every ~0.1 ms) and passes it on to the
+                                 kernels, which check it before each work item; the handle
+                                 stays usable and the next md_compute starts afresh */
     int batch_mode;           /* md_batch only: 0 (default) = all codes in one persistent
                                  round schedule; 1 = one md_compute per code, in order */
     int use_graph;            /* md_batch only: 1 (default) = capture the round schedule in a
@@ -108,6 +112,17 @@ typedef struct md_options {
                                  MMA issuers' bounded wait (4 s) runs out: each block frees
                                  its tensor memory and returns, the run stops, and
                                  md_compute returns MD_ETIMEOUT with the context intact */
+    /* Optional device allocator for the library's device buffers (md_compute's per-handle
+       buffer, md_scan_task's work table, md_batch's engine tables and code arena), for
+       callers whose device memory belongs to another allocator.  dev_alloc returns device
+       memory of at least `bytes` bytes aligned to 256 bytes, or NULL on failure (the call
+       then returns MD_ENOMEM); dev_free releases it.  Both are called from the thread that
+       calls the library, with alloc_ctx.  NULL = cudaMalloc / cudaFree.  Memory is released
+       by md_destroy (md_compute) or before the call returns (md_scan_task, md_batch); the
+       caller keeps the allocator valid until then. */
+    void *(*dev_alloc)(size_t bytes, void *alloc_ctx);
+    void (*dev_free)(void *ptr, void *alloc_ctx);
+    void *alloc_ctx;
 } md_options;
 
 /* Result details of the last md_compute on a handle. */

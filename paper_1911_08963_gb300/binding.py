@@ -31,7 +31,12 @@ class md_options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("cancel_flag", ctypes.POINTER(ctypes.c_int)),
                 ("batch_mode", ctypes.c_int), ("use_graph", ctypes.c_int), ("plan_horizon", ctypes.c_int),
                 ("stop_rule", ctypes.c_int), ("perm_trials", ctypes.c_int), ("perm_seed", ctypes.c_uint64),
-                ("tensor", ctypes.c_int), ("tensor_head", ctypes.c_int), ("test_stall", ctypes.c_int)]
+                ("tensor", ctypes.c_int), ("tensor_head", ctypes.c_int), ("test_stall", ctypes.c_int),
+                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p)]
+
+# Prototypes of the allocator hook (md_options.dev_alloc / dev_free).
+DEV_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+DEV_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
 
 
 class md_info(ctypes.Structure):

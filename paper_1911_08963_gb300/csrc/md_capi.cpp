@@ -9,6 +9,7 @@
 #include <chrono>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "md_internal.h"
@@ -58,12 +59,39 @@ struct md_ctx {
     int smem_optin = 0;
     int setup_launches = 0;                 // device setup work charged to the next compute
     uint64_t setup_h2d = 0;
+    volatile int *cancel_host = nullptr;    // mapped pinned word the kernels poll per work item
+    const volatile int *cancel_dev = nullptr;
 };
 
 namespace {
 
 cudaStream_t stream_of(md_ctx *h) {
     return h->opt.stream ? (cudaStream_t)h->opt.stream : h->own_stream;
+}
+
+// Device memory through the caller's allocator (md_options.dev_alloc), else cudaMalloc.
+void *dev_malloc(const md_options &o, size_t bytes) {
+    if (o.dev_alloc) return o.dev_alloc(bytes, o.alloc_ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return p;
+}
+void dev_release(const md_options &o, void *p) {
+    if (!p) return;
+    if (o.dev_free) o.dev_free(p, o.alloc_ctx);
+    else cudaFree(p);
+}
+
+// Wait for an event.  With a cancel flag, poll instead of blocking and pass the flag on to the
+// kernels, which stop before their next work item.
+cudaError_t wait_event(md_ctx *h, cudaEvent_t e) {
+    if (!h->opt.cancel_flag || !h->cancel_host) return cudaEventSynchronize(e);
+    for (;;) {
+        const cudaError_t q = cudaEventQuery(e);
+        if (q != cudaErrorNotReady) return q;
+        if (*h->opt.cancel_flag) *h->cancel_host = 1;
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
 }
 
 void fill_static_info(md_ctx *h) {
@@ -76,8 +104,14 @@ void fill_static_info(md_ctx *h) {
 }
 
 void free_device(md_ctx *h) {
-    if (h->dev.base) cudaFree(h->dev.base);
+    if (h->dev.base) {
+        cudaStreamSynchronize(stream_of(h));        // a caller's free need not wait for our kernels
+        dev_release(h->opt, h->dev.base);
+    }
     h->dev = DevLayout();
+    if (h->cancel_host) cudaFreeHost((void *)h->cancel_host);
+    h->cancel_host = nullptr;
+    h->cancel_dev = nullptr;
     if (h->host_state) cudaFreeHost(h->host_state);
     h->host_state = nullptr;
     if (h->heads) cudaFreeHost(h->heads);
@@ -161,7 +195,18 @@ int setup_device(md_ctx *h) {
     const size_t st_off = off;
     off = align256(off + sizeof(DevState));
 
-    if (cudaMalloc(&h->dev.base, off) != cudaSuccess) { cudaGetLastError(); free_device(h); return MD_ENOMEM; }
+    h->dev.base = (char *)dev_malloc(h->opt, off);
+    if (!h->dev.base) { free_device(h); return MD_ENOMEM; }
+    if (((uintptr_t)h->dev.base & 255) != 0) { free_device(h); return MD_EINVAL; }   // the hook's alignment
+    {
+        // the cancel word: mapped pinned memory, read by the kernels through its device address
+        void *cw = nullptr, *cwd = nullptr;
+        if (cudaHostAlloc(&cw, 64, cudaHostAllocMapped) != cudaSuccess) { cudaGetLastError(); free_device(h); return MD_ENOMEM; }
+        h->cancel_host = (volatile int *)cw;
+        *h->cancel_host = 0;
+        if (cudaHostGetDevicePointer(&cwd, cw, 0) != cudaSuccess) { cudaGetLastError(); free_device(h); return MD_ECUDA; }
+        h->cancel_dev = (const volatile int *)cwd;
+    }
     if (cudaMallocHost(&h->host_state, sizeof(DevState)) != cudaSuccess ||
         cudaMallocHost(&h->heads, sizeof(md_ctx::Head) * std::max(1, h->g_limit)) != cudaSuccess) {
         cudaGetLastError();
@@ -277,6 +322,7 @@ LevelArgs level_args(md_ctx *h, const LevelPlan &p, int level, bool h2s) {
     a.L_after = p.L_after;
     a.L_first = p.L_first;
     a.check_stop = 1;
+    a.cancel = h->cancel_dev;
     (void)gm;
     return a;
 }
@@ -374,6 +420,7 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
 
     cudaEvent_t ev0 = h->run_ev[0], ev1 = h->run_ev[1];
     using Head = md_ctx::Head;
+    *h->cancel_host = 0;                  // a cancelled run left it set
     int nlev_ev = 0, nstages = 0;
     int launches = 0;
     uint64_t h2d = 0, d2h = 0;
@@ -409,7 +456,8 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
                 a = level_args(h, p, level, false);
                 err |= launch_tc_level(h->dev.heads[p.j], h->dev.heads2[p.j], p.tc_smin, h->dev.rows[p.j],
                                        h->dev.binom, h->dev.st, k, p.g, p.tc_q, p.base, level, c.gam[p.j].W,
-                                       c.gam[p.j].WP, 1, h->sms, h->opt.test_stall, p.tc_words8, s) != 0;
+                                       c.gam[p.j].WP, 1, h->sms, h->opt.test_stall, p.tc_words8, h->cancel_dev,
+                                       s) != 0;
             } else {
                 LaunchCfg L = launch_cfg(h, p);
                 a = level_args(h, p, level, L.h2s);
@@ -427,12 +475,12 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
         nstages++;
         // look one stage behind: the device keeps working on the stage just queued
         if (nstages >= 2) {
-            cudaEventSynchronize(h->stage_ev[nstages - 2]);
+            wait_event(h, h->stage_ev[nstages - 2]);
             if (h->heads[nstages - 2].stop) { stopped = true; break; }
         }
     }
     cudaEventRecord(ev1, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) err = true;
+    if (wait_event(h, ev1) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) err = true;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
     std::vector<double> lev_sec(nlev_ev / 2, 0.0);
@@ -444,7 +492,7 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
     if (cudaMemcpy(h->host_state, h->dev.st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) return MD_ECUDA;
     d2h += sizeof(DevState);
     const DevState &st = *h->host_state;
-    if (st.error) return st.error == MD_ETIMEOUT ? MD_ETIMEOUT : MD_EINTERNAL;
+    if (st.error) return st.error == MD_ETIMEOUT || st.error == MD_ECANCELED ? st.error : MD_EINTERNAL;
     // complete: L >= U was reached, or every stage up to g = k ran (Alg. 1's loop bound)
     stopped = st.stop != 0 || (status == MD_OK && st.last_level == k * m - 1);
 
@@ -573,6 +621,7 @@ int md_scan_range(md_handle h, int g, int j, uint64_t r0, uint64_t r1, int bound
     a.r_begin = r0;
     a.count = r1;
     a.check_stop = 0;
+    a.cancel = nullptr;                   // scans are not cancelled
     const unsigned u0 = bound >= 0 ? (unsigned)bound : (unsigned)(c.n + 1);
     bool err = launch_state_init(h->dev.st, u0, s) != 0;
     if (span > 0) err |= launch_level(a, p.kind, c.gam[j].W, c.gam[j].WP, L.blocks, L.threads, L.smem, s) != 0;
@@ -619,20 +668,21 @@ int md_scan_task(md_handle h, int g, int j, int M, uint64_t u0, uint64_t u1, int
     p.mtab.assign(1, e);
     p.nchunks = (e.uppers + 32ull * per_lane - 1) / (32ull * per_lane);
     // the task's work table lives in the spare entry past the planned levels
-    MEntry *dtab = nullptr;
-    if (cudaMalloc(&dtab, sizeof(MEntry)) != cudaSuccess) { cudaGetLastError(); return MD_ENOMEM; }
+    MEntry *dtab = (MEntry *)dev_malloc(h->opt, 256);
+    if (!dtab) return MD_ENOMEM;
     bool err = cudaMemcpy(dtab, &e, sizeof(MEntry), cudaMemcpyHostToDevice) != cudaSuccess;
     LaunchCfg L = launch_cfg(h, p);
     LevelArgs a = level_args(h, p, 0, L.h2s);
     a.mtab = dtab;
     a.check_stop = 0;
+    a.cancel = nullptr;
     const unsigned ub = bound >= 0 ? (unsigned)bound : (unsigned)(c.n + 1);
     err |= launch_state_init(h->dev.st, ub, s) != 0;
     if (p.nchunks > 0) err |= launch_level(a, p.kind, c.gam[j].W, c.gam[j].WP, L.blocks, L.threads, L.smem, s) != 0;
     unsigned long long key = kNoKey;
     if (!err) err = cudaMemcpyAsync(&key, &h->dev.st->key[0], 8, cudaMemcpyDeviceToHost, s) != cudaSuccess;
     if (cudaStreamSynchronize(s) != cudaSuccess) err = true;
-    cudaFree(dtab);
+    dev_release(h->opt, dtab);
     if (err) { cudaGetLastError(); return MD_ECUDA; }
     if (key == kNoKey) { *weight = -1; *first_rank = 0; }
     else { *weight = (int)(key >> kRankBits); *first_rank = key & (kRankLimit - 1); }

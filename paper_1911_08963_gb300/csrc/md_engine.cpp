@@ -74,6 +74,22 @@ void prepare_codes(const md_code *codes, int count, const PlanOptions &po, int m
 
 Engine::~Engine() { release_all(); }
 
+void *Engine::dmalloc(size_t bytes) {
+    if (alloc_) {
+        void *p = alloc_(bytes, alloc_ctx_);
+        return ((uintptr_t)p & 255) == 0 ? p : nullptr;     // the hook promises 256-byte alignment
+    }
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return p;
+}
+
+void Engine::dfree(void *p) {
+    if (!p) return;
+    if (free_) free_(p, alloc_ctx_);
+    else cudaFree(p);
+}
+
 int Engine::init(int nslots, cudaStream_t stream, unsigned long long quota, int blocks_per_sm_cap) {
     stream_ = stream;
     nslots_ = nslots;
@@ -92,7 +108,8 @@ int Engine::init(int nslots, cudaStream_t stream, unsigned long long quota, int 
     const size_t tot_off = off; off = align256(off + kWClasses * 8);
     const size_t ctr_off = off; off = align256(off + kWClasses * 8);
     const size_t bin_off = off; off = align256(off + (size_t)257 * 257 * 8);
-    if (cudaMalloc(&tables_, off) != cudaSuccess) { cudaGetLastError(); tables_ = nullptr; return MD_ENOMEM; }
+    tables_ = (char *)dmalloc(off);
+    if (!tables_) return MD_ENOMEM;
     if (cudaMemsetAsync(tables_, 0, off, stream_) != cudaSuccess) return MD_ECUDA;
     std::vector<unsigned long long> tb((size_t)257 * 257);
     for (int a = 0; a <= 256; a++)
@@ -198,11 +215,9 @@ int Engine::write_slot(int slot, const BCode &bc, const BState &bs) {
 
 // Build the pair tables of the given matrices (groups of up to 256 per launch).
 static int build_pair_tables(const std::vector<const uint32_t *> &rp, const std::vector<uint32_t *> &hp,
-                             const std::vector<int> &kk, const std::vector<int> &wp, cudaStream_t s) {
+                             const std::vector<int> &kk, const std::vector<int> &wp, cudaStream_t s, char *ptrs) {
     if (rp.empty()) return MD_OK;
-    char *ptrs = nullptr;
     const size_t bytes = (size_t)2 * 256 * 8 + 2 * 256 * 4;
-    if (cudaMalloc(&ptrs, bytes) != cudaSuccess) { cudaGetLastError(); return MD_ENOMEM; }
     int rc = MD_OK;
     for (size_t g0 = 0; g0 < rp.size() && rc == MD_OK; g0 += 256) {
         const int cnt = (int)std::min<size_t>(256, rp.size() - g0);
@@ -219,7 +234,6 @@ static int build_pair_tables(const std::vector<const uint32_t *> &rp, const std:
         else if (cudaStreamSynchronize(s) != cudaSuccess)
             rc = MD_ECUDA;
     }
-    cudaFree(ptrs);
     return rc;
 }
 
@@ -246,8 +260,10 @@ int Engine::load_many(const std::vector<PreparedCode *> &codes, const std::vecto
         hb += p->header_bytes;
         h2b += p->h2_bytes;
     }
-    char *mem = nullptr;
-    if (cudaMalloc(&mem, std::max<size_t>(256, hb + h2b)) != cudaSuccess) { cudaGetLastError(); return MD_ENOMEM; }
+    // one allocation: headers, pair tables, and the pointer block of the pair-table builds
+    const size_t ptr_off = align256(hb + h2b);
+    char *mem = (char *)dmalloc(ptr_off + (size_t)2 * 256 * 8 + 2 * 256 * 4);
+    if (!mem) return MD_ENOMEM;
     shared_mem_.push_back(mem);
     std::vector<char> img(hb, 0);
     std::vector<BCode> bcs(codes.size());
@@ -270,7 +286,7 @@ int Engine::load_many(const std::vector<PreparedCode *> &codes, const std::vecto
         h2off += pc.h2_bytes;
     }
     if (cudaMemcpyAsync(mem, img.data(), hb, cudaMemcpyHostToDevice, stream_) != cudaSuccess) return MD_ECUDA;
-    int rc = build_pair_tables(rp, hp, kk, wp, stream_);
+    int rc = build_pair_tables(rp, hp, kk, wp, stream_, mem + ptr_off);
     if (rc != MD_OK) return rc;
     std::vector<BState> bss(codes.size());
     for (size_t i = 0; i < codes.size(); i++) {
@@ -419,9 +435,9 @@ void Engine::release_all() {
     for (char *&p : own_mem_)
         if (p) { cudaFreeAsync(p, stream_); p = nullptr; }
     if (stream_) cudaStreamSynchronize(stream_);
-    for (char *p : shared_mem_) cudaFree(p);
+    for (char *p : shared_mem_) dfree(p);
     shared_mem_.clear();
-    if (tables_) cudaFree(tables_);
+    dfree(tables_);
     tables_ = nullptr;
     stream_ = nullptr;                 // the stream belongs to the caller
 }
@@ -512,6 +528,7 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
     int rc;
     {
         Engine eng;
+        eng.set_allocator(o.dev_alloc, o.dev_free, o.alloc_ctx);
         rc = eng.init(nc, s, 0, o.blocks_per_sm);
         std::vector<int> slots(nc);
         for (int i = 0; i < nc; i++) slots[i] = i;

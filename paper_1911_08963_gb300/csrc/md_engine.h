@@ -67,6 +67,14 @@ class Engine {
     int release(int slot);
     void release_all();
 
+    // Device allocations of init and load_many through the caller's allocator (md_options
+    // dev_alloc / dev_free); set before init.  Unset: cudaMalloc / cudaFree.
+    void set_allocator(void *(*alloc)(size_t, void *), void (*release)(void *, void *), void *ctx) {
+        alloc_ = alloc;
+        free_ = release;
+        alloc_ctx_ = ctx;
+    }
+
     int nslots() const { return nslots_; }
     cudaStream_t stream() const { return stream_; }
     int launches() const { return launches_; }
@@ -92,7 +100,12 @@ class Engine {
     unsigned graph_mask_ = 0;
     int graph_repeats_ = 0;
     int enqueue_ticks(int repeats);
+    void *dmalloc(size_t bytes);
+    void dfree(void *p);
     std::vector<BCode> host_codes_;
+    void *(*alloc_)(size_t, void *) = nullptr;
+    void (*free_)(void *, void *) = nullptr;
+    void *alloc_ctx_ = nullptr;
 };
 
 }  // namespace mdl

@@ -164,6 +164,7 @@ struct LevelArgs {
     int L_after;
     int L_first;
     int check_stop;                 // 0 for md_scan_range (no stop logic)
+    const volatile int *cancel;     // non-zero: stop before the next work item (null: none)
 };
 
 // ---- many codes: the engine behind md_batch and the server (md_engine.cu) ----
@@ -230,7 +231,8 @@ int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, in
 // words8: the product's word counts per threshold (LevelPlan::tc_words8).
 int launch_tc_level(const unsigned char *tables, const unsigned char *tables2, int smin, const uint32_t *rows,
                     const unsigned long long *binom_d, DevState *st, int k, int g, int q, int base, int level, int W,
-                    int WP, int check_stop, int blocks, int stall, unsigned long long words8, void *stream);
+                    int WP, int check_stop, int blocks, int stall, unsigned long long words8,
+                    const volatile int *cancel, void *stream);
 int launch_level(const LevelArgs &a, int kind, int W, int WP, int blocks, int threads, size_t smem,
                  void *stream);
 int launch_finalize(const LevelArgs &a, void *stream);

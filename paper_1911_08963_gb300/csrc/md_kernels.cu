@@ -36,6 +36,23 @@ namespace {
 using namespace dev;
 constexpr int kThreads = 512;
 
+// The warp's next work item of the level (lane 0 takes a ticket, the warp shares it), or
+// ~0 once the caller cancels the run: the cancel word (mapped host memory) is read before
+// every ticket, and a cancelled run is stopped with MD_ECANCELED for the levels after it.
+__device__ __forceinline__ unsigned long long next_item(const LevelArgs &a, int lane) {
+    unsigned long long chunk = 0;
+    if (lane == 0) {
+        if (a.cancel && *a.cancel) {
+            atomicExch(&a.st->error, MD_ECANCELED);
+            atomicExch(&a.st->stop, 1);
+            chunk = ~0ull;
+        } else {
+            chunk = atomicAdd(&a.st->ctr[a.level], 1ull);
+        }
+    }
+    return __shfl_sync(kFull, chunk, 0);
+}
+
 // ---------------------------------------------------------------- split kernel ----
 // One level (g, j) of one code.  The packed rows of Gamma_j are staged in shared memory
 // once per block, with the pair table too when it fits (H2S); warps then take work items
@@ -59,9 +76,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_kernel(const LevelArgs a) {
     int Usnap = (int)*(volatile unsigned int *)&st->U;
 
     for (;;) {
-        unsigned long long chunk = 0;
-        if (lane == 0) chunk = atomicAdd(&st->ctr[a.level], 1ull);
-        chunk = __shfl_sync(kFull, chunk, 0);
+        const unsigned long long chunk = next_item(a, lane);
         if (chunk >= a.nchunks) break;
         const MEntry e = a.mtab[find_entry(a.mtab, a.n_m, chunk)];
         LaneBest best;
@@ -93,9 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1) simple_kernel(const LevelArgs a) 
     const int lane = threadIdx.x & 31;
     int Usnap = (int)*(volatile unsigned int *)&st->U;
     for (;;) {
-        unsigned long long chunk = 0;
-        if (lane == 0) chunk = atomicAdd(&st->ctr[a.level], 1ull);
-        chunk = __shfl_sync(kFull, chunk, 0);
+        const unsigned long long chunk = next_item(a, lane);
         if (chunk >= a.nchunks) break;
         const unsigned long long lo = a.r_begin + (chunk * 32ull + (unsigned long long)lane) * a.per_chunk;
         const unsigned long long hi = min(lo + a.per_chunk, (unsigned long long)a.count);

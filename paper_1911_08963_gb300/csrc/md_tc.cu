@@ -368,6 +368,7 @@ struct TcArgs {
     // which f words still reject all but a tiny fraction of codewords (0 = never; the byte of
     // f = W, the exact product, is 255).  An item takes the fewest qualifying words.
     unsigned long long words8;
+    const volatile int *cancel;            // non-zero: hand out no more items (null: none)
 };
 
 __device__ __forceinline__ unsigned long long C(const TcArgs &a, int n, int r) {
@@ -630,6 +631,12 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                 if (use >= 1 && !mbar_wait(saddr(&sh.ifree[slot]), (use - 1) & 1, abort_flag)) break;
                 TcItem it{};
                 for (;;) {
+                    if (a.cancel && *a.cancel) {                // the caller cancelled the run
+                        atomicExch(&st->error, MD_ECANCELED);
+                        atomicExch(&st->stop, 1);
+                        it.end = 1;
+                        break;
+                    }
                     unsigned long long idx = atomicAdd(&st->ctr[a.level], 1ull);
                     if (idx >= total) { it.end = 1; break; }
                     const int ph = idx >= total0 ? 1 : 0;
@@ -1079,14 +1086,15 @@ int launch_tc_tables(const uint32_t *rows, const unsigned long long *binom_d, in
 
 int launch_tc_level(const unsigned char *tables, const unsigned char *tables2, int smin, const uint32_t *rows,
                     const unsigned long long *binom_d, DevState *st, int k, int g, int q, int base, int level, int W,
-                    int WP, int check_stop, int blocks, int stall, unsigned long long words8, void *stream) {
+                    int WP, int check_stop, int blocks, int stall, unsigned long long words8,
+                    const volatile int *cancel, void *stream) {
     int dev = 0, optin = 0, with_bsub = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
         return (int)cudaErrorInvalidValue;
     const size_t smem = (size_t)tc_smem_bytes(k, W, optin, &with_bsub);
     TcArgs a{{tables, tables2}, rows, binom_d, st, k, g, q, base, level, WP, tc_tiles_per_set(W), check_stop,
-             with_bsub, smin, stall, words8};
+             with_bsub, smin, stall, words8, cancel};
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
     switch (W) {
