@@ -123,6 +123,14 @@ typedef struct md_options {
     void *(*dev_alloc)(size_t bytes, void *alloc_ctx);
     void (*dev_free)(void *ptr, void *alloc_ctx);
     void *alloc_ctx;
+    uint64_t batch_heavy;     /* md_batch: codes whose estimated work (combinations until L >= U
+                                 for a random code of that shape) reaches this run one by one
+                                 as single-code computations, with the tensor-core levels, after
+                                 the shared schedule of the others (such a code fills the GPU by
+                                 itself); 0 = default 2^34, UINT64_MAX = none */
+    int autotune;             /* md_batch: 1 = first pick chunk_log2, blocks_per_sm and batch_heavy
+                                 with md_batch_tune (cached in tune_cache when set) */
+    const char *tune_cache;   /* md_batch_tune's JSON cache file (NULL = no cache) */
 } md_options;
 
 /* Result details of the last md_compute on a handle. */
@@ -283,6 +291,27 @@ typedef struct md_code {
 
 int md_batch(const md_code *codes, int count, const md_options *opt,
              int *d, uint64_t *witness, int *status);
+
+/* ---- autotuning of md_batch ----------------------------------------------------------
+ * md_batch_tune picks md_batch's schedule options for batches shaped like codes[0..count) on
+ * the current GPU: the combinations per work item (chunk_log2 in {16, 18, 20}), the blocks per
+ * SM of the shared rounds ({occupancy, 2, 4}), and the single-code threshold (batch_heavy in
+ * {2^30, 2^32, ..., 2^38}).  It times md_batch on deterministic samples of the batch (every
+ * i-th code): up to 384 codes of estimated work below 2^34 for the first two, then up to 24
+ * codes between 2^30 and 2^38 for the threshold, and writes into *tuned a copy of *base
+ * (defaults if NULL) with the fastest values.  With cache_path, the choice is stored in that
+ * JSON file under the key md_batch_tune_key(...) + " | " + the GPU's name, and a later call
+ * with the same key reads it back without timing anything.  Codes over base->work_budget
+ * are left out of the samples.  Returns MD_OK, MD_EINVAL (bad arguments, unwritable cache),
+ * MD_ECUDA (no GPU) or the error of a timing run.  The paper's own tuning is the choice of
+ * prefix size and threads per process (Section 4); these knobs are this library's analogue.
+ */
+int md_batch_tune(const md_code *codes, int count, const md_options *base, const char *cache_path,
+                  md_options *tuned);
+
+/* The batch-shape part of the tuning key: "n<lo>-<hi> k<lo>-<hi> c2^<e>" with n rounded out to
+   multiples of 16, k to multiples of 8, and count to the next power of two.  Host only. */
+int md_batch_tune_key(const md_code *codes, int count, char *key, size_t len);
 
 /* ---- continuous-batching server -------------------------------------------------------
  * A server owns a device region for resident codes and a host thread that admits

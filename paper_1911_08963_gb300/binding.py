@@ -32,7 +32,8 @@ class md_options(ctypes.Structure):
                 ("batch_mode", ctypes.c_int), ("use_graph", ctypes.c_int), ("plan_horizon", ctypes.c_int),
                 ("stop_rule", ctypes.c_int), ("perm_trials", ctypes.c_int), ("perm_seed", ctypes.c_uint64),
                 ("tensor", ctypes.c_int), ("tensor_head", ctypes.c_int), ("test_stall", ctypes.c_int),
-                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p)]
+                ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p),
+                ("batch_heavy", ctypes.c_uint64), ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
 
 # Prototypes of the allocator hook (md_options.dev_alloc / dev_free).
 DEV_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
@@ -89,6 +90,9 @@ PROTOTYPES = {
     "md_destroy": (None, [ctypes.c_void_p]),
     "md_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "md_batch": (ctypes.c_int, [ctypes.POINTER(md_code), ctypes.c_int, ctypes.POINTER(md_options), ip, u64p, ip]),
+    "md_batch_tune": (ctypes.c_int, [ctypes.POINTER(md_code), ctypes.c_int, ctypes.POINTER(md_options),
+                                     ctypes.c_char_p, ctypes.POINTER(md_options)]),
+    "md_batch_tune_key": (ctypes.c_int, [ctypes.POINTER(md_code), ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t]),
     "md_server_create": (ctypes.c_int, [ctypes.POINTER(md_server_opts), ctypes.POINTER(ctypes.c_void_p)]),
     "md_server_submit": (ctypes.c_int, [ctypes.c_void_p, u64p, ctypes.c_int, ctypes.c_int, u64p]),
     "md_server_poll": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_uint64, ip, u64p, ip]),
@@ -219,16 +223,39 @@ def md_destroy(h: int) -> None:
         lib.md_destroy(h)
 
 
-def md_batch(codes, options: md_options | None = None):
-    """codes: list of (G, n, k).  Returns (d list, witnesses list, status list)."""
+def _code_array(codes):
+    """ctypes md_code array of [(G, n, k)] and the numpy rows it points into (keep alive)."""
     arr = (md_code * len(codes))()
     keep = []
-    offs = []
-    total = 0
     for i, (G, n, k) in enumerate(codes):
         G, p = _rows(G, n, k)
         keep.append(G)
         arr[i].G, arr[i].n, arr[i].k = p, n, k
+    return arr, keep
+
+
+def md_batch_tune(codes, options: md_options | None = None, cache_path: str | None = None) -> md_options:
+    """The tuned copy of `options` (see include/md.h)."""
+    arr, keep = _code_array(codes)
+    out = md_options()
+    _check(lib.md_batch_tune(arr, len(codes), ctypes.byref(options) if options is not None else None,
+                             cache_path.encode() if cache_path else None, ctypes.byref(out)), "md_batch_tune")
+    return out
+
+
+def md_batch_tune_key(codes) -> str:
+    arr, keep = _code_array(codes)
+    buf = ctypes.create_string_buffer(256)
+    _check(lib.md_batch_tune_key(arr, len(codes), buf, 256), "md_batch_tune_key")
+    return buf.value.decode()
+
+
+def md_batch(codes, options: md_options | None = None):
+    """codes: list of (G, n, k).  Returns (d list, witnesses list, status list)."""
+    arr, keep = _code_array(codes)
+    offs = []
+    total = 0
+    for G, n, k in codes:
         offs.append(total)
         total += (n + 63) // 64
     d = (ctypes.c_int * len(codes))()

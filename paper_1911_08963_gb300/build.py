@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libmd.so")
-SOURCES = ["md_kernels.cu", "md_engine.cu", "md_host.cpp", "md_capi.cpp", "md_engine.cpp", "md_server.cpp", "md_noalloc.cu", "md_tc.cu"]
+SOURCES = ["md_kernels.cu", "md_engine.cu", "md_host.cpp", "md_capi.cpp", "md_engine.cpp", "md_server.cpp", "md_noalloc.cu",
+           "md_tc.cu", "md_tune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 # extra nvcc flags for tuning experiments (e.g. -DMD_UPPERS_PER_LANE=4); empty by default

@@ -23,6 +23,7 @@ int prepare_code(const uint64_t *G, int n, int k, const PlanOptions &po, int max
     int g_est = 0;
     const double work = estimate_work(p.code, nullptr, &g_est);
     if (budget && work > (double)budget) return MD_EBUDGET;
+    p.est_work = work;
     const int m = (int)p.code.gam.size();
     for (int g = 1; g <= std::min(k, kMaxG); g++) {
         if (binom(k, g) >= kRankLimit) break;
@@ -481,6 +482,26 @@ int per_code_loop(const md_code *codes, int count, const md_options &o, int *d, 
     return MD_OK;
 }
 
+// One code as a single-code computation (md_compute, with the tensor-core levels the options
+// allow) on stream s: its status, d and witness.
+int single_code_run(const md_code &c, const md_options &o, cudaStream_t s, int *d, uint64_t *witness) {
+    md_options oi = o;
+    oi.stream = s;
+    oi.work_budget = 0;                      // the batch's budget was applied to the estimate
+    md_handle h = nullptr;
+    int di = -1;
+    int rc = md_create_ex(c.G, c.n, c.k, &oi, &h);
+    if (rc == MD_OK) rc = md_compute(h, &di, witness);
+    if (rc == MD_OK) {
+        md_info inf;
+        md_info_get(h, &inf);
+        if (!inf.complete) rc = MD_EBUDGET;    // stopped by max_stage: d is the best weight found
+    }
+    if (h) md_destroy(h);
+    *d = rc == MD_OK || rc == MD_EBUDGET ? di : -1;
+    return rc;
+}
+
 }  // namespace
 
 extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, int *d, uint64_t *witness,
@@ -490,6 +511,12 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
     md_options o;
     if (opt) o = *opt; else md_options_init(&o);
     if (o.batch_mode == 1) return per_code_loop(codes, count, o, d, witness, status);
+    if (o.autotune) {
+        md_options base = o;
+        base.autotune = 0;
+        const int rc = md_batch_tune(codes, count, &base, o.tune_cache, &o);
+        if (rc != MD_OK) return rc;
+    }
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) { cudaGetLastError(); return MD_ECUDA; }
 
@@ -502,31 +529,38 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
     std::vector<PreparedCode> prep;
     std::vector<size_t> woffs(count);
     std::vector<PreparedCode *> ok_codes;
-    std::vector<int> ok_index;
+    std::vector<int> ok_index, heavy_index;
     size_t wtot = 0;
     int rounds = 0;
     prepare_codes(codes, count, po, o.max_stage, o.work_budget, prep, status,
                   o.plan_horizon > 0 ? o.plan_horizon : 3);
+    // codes whose estimated work reaches batch_heavy fill the GPU on their own: they run as
+    // single-code computations (with the tensor-core levels) after the shared schedule
+    const double heavy = o.batch_heavy ? (double)o.batch_heavy : (double)kBatchHeavyDefault;
     for (int i = 0; i < count; i++) {
         woffs[i] = wtot;
         wtot += codes[i].n > 0 ? (size_t)(codes[i].n + 63) / 64 : 0;
         d[i] = -1;
-        if (status[i] == MD_OK) {
-            ok_codes.push_back(&prep[i]);
-            ok_index.push_back(i);
-            rounds = std::max(rounds, (int)prep[i].plans.size());
+        if (status[i] != MD_OK) continue;
+        if (prep[i].est_work >= heavy) {
+            heavy_index.push_back(i);
+            prep[i] = PreparedCode();          // its plans are not needed
+            continue;
         }
+        ok_codes.push_back(&prep[i]);
+        ok_index.push_back(i);
+        rounds = std::max(rounds, (int)prep[i].plans.size());
     }
     const int nc = (int)ok_codes.size();
-    if (nc == 0) return MD_OK;
+    if (nc == 0 && heavy_index.empty()) return MD_OK;
     cudaStream_t s = (cudaStream_t)o.stream;
     cudaStream_t own = nullptr;
     if (!s) {
         if (cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking) != cudaSuccess) return MD_ECUDA;
         s = own;
     }
-    int rc;
-    {
+    int rc = MD_OK;
+    if (nc > 0) {
         Engine eng;
         eng.set_allocator(o.dev_alloc, o.dev_free, o.alloc_ctx);
         rc = eng.init(nc, s, 0, o.blocks_per_sm);
@@ -558,20 +592,7 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
             const int i = ok_index[c];
             if (res.status == MD_EAGAIN_INTERNAL) {
                 // rare: the run went past the planned stages; finish it as a single code
-                md_options oi = o;
-                oi.stream = s;
-                md_handle h = nullptr;
-                int di = -1;
-                int r2 = md_create_ex(codes[i].G, codes[i].n, codes[i].k, &oi, &h);
-                if (r2 == MD_OK) r2 = md_compute(h, &di, witness ? witness + woffs[i] : nullptr);
-                if (r2 == MD_OK) {
-                    md_info inf;
-                    md_info_get(h, &inf);
-                    if (!inf.complete) r2 = MD_EBUDGET;
-                }
-                if (h) md_destroy(h);
-                status[i] = r2;
-                d[i] = r2 == MD_OK || r2 == MD_EBUDGET ? di : -1;
+                status[i] = single_code_run(codes[i], o, s, &d[i], witness ? witness + woffs[i] : nullptr);
                 continue;
             }
             status[i] = res.status;
@@ -580,6 +601,11 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
                 if (witness) std::memcpy(witness + woffs[i], res.witness.data(), res.witness.size() * 8);
             }
         }
+    }
+    for (size_t h = 0; rc == MD_OK && h < heavy_index.size(); h++) {
+        const int i = heavy_index[h];
+        status[i] = single_code_run(codes[i], o, s, &d[i], witness ? witness + woffs[i] : nullptr);
+        if (status[i] == MD_ECUDA || status[i] == MD_ENOMEM) rc = status[i];
     }
     if (own) cudaStreamDestroy(own);
     return rc;

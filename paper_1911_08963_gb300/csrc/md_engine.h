@@ -18,6 +18,7 @@ struct PreparedCode {
     int max_stage = 0;
     size_t header_bytes = 0;        // rows, level table, work tables, keys
     size_t h2_bytes = 0;            // pair tables
+    double est_work = 0.0;          // estimated combinations until L >= U (estimate_work)
 };
 
 // Validate G, build the Gamma_j, check the work budget (estimated combinations) and plan

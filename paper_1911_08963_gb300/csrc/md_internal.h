@@ -21,6 +21,7 @@ constexpr int kRankBits = 55;                 // level key = weight << 55 | cole
 constexpr uint64_t kRankLimit = 1ull << kRankBits;
 constexpr uint64_t kNoKey = ~0ull;
 constexpr int MD_EAGAIN_INTERNAL = 100;       // engine: the run needs stages past its plan
+constexpr uint64_t kBatchHeavyDefault = 1ull << 34;   // md_batch: single-code runs from this estimated work
 
 // -------------------------------------------------------------------- host side ---
 

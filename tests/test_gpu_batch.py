@@ -105,3 +105,59 @@ def test_batch_per_matrix_bound(B):
     for (G, n, k), di, wi in zip(codes, d1, w1):
         res = O.bz(G, n, k, threads=8, stop_rule=1)
         assert di == res.d and np.array_equal(wi, res.witness)
+
+
+@pytest.mark.parametrize("heavy", [1 << 12, 1 << 20, (1 << 64) - 1])
+def test_batch_heavy_codes_run_alone(B, heavy):
+    """Codes whose estimated work reaches batch_heavy run one by one as single-code
+    computations (tensor-core levels forced on, so the small codes here reach that kernel too)
+    after the shared schedule of the others; every result equals the oracle's, whichever
+    route each code takes (2^12: most codes alone; 2^20: a mix; 2^64 - 1: none)."""
+    codes = mixed_codes()
+    d, wits, st = B.md_batch(codes, B.md_options_init(batch_heavy=heavy, tensor=2))
+    assert st == [B.MD_OK] * len(codes)
+    for (G, n, k), di, wi in zip(codes, d, wits):
+        res = O.bz(G, n, k, threads=8)
+        assert di == res.d and np.array_equal(wi, res.witness), (n, k, heavy)
+
+
+def test_batch_tune_picks_cached_valid_options(B, tmp_path):
+    """md_batch_tune times md_batch on samples of the batch, writes its choice to the JSON
+    cache under the batch's key and the GPU's name, and reads it back on the next call without
+    timing; md_batch with the tuned options (and with autotune = 1 through the cache) gives
+    exactly the default options' results, which the oracle confirms on the small codes."""
+    import json
+    import time
+    codes = I.batch_codes(count=256)
+    base = B.md_options_init(work_budget=10 ** 9)
+    cache = str(tmp_path / "tune.json")
+    t0 = time.perf_counter()
+    tuned = B.md_batch_tune(codes, base, cache)
+    first = time.perf_counter() - t0
+    assert tuned.chunk_log2 in (16, 18, 20) and tuned.blocks_per_sm in (0, 2, 4)
+    assert tuned.batch_heavy in [1 << e for e in (30, 32, 34, 36, 38)]
+    assert tuned.work_budget == 10 ** 9
+    entries = json.load(open(cache))
+    key = B.md_batch_tune_key(codes)
+    (name, val), = entries.items()
+    assert name.startswith(key + " | ")
+    assert (val["chunk_log2"], val["blocks_per_sm"], val["batch_heavy"]) == \
+        (tuned.chunk_log2, tuned.blocks_per_sm, tuned.batch_heavy)
+    t0 = time.perf_counter()
+    again = B.md_batch_tune(codes, base, cache)
+    assert time.perf_counter() - t0 < first / 5
+    assert (again.chunk_log2, again.blocks_per_sm, again.batch_heavy) == \
+        (tuned.chunk_log2, tuned.blocks_per_sm, tuned.batch_heavy)
+    ref = B.md_batch(codes, base)
+    got = B.md_batch(codes, tuned)
+    auto = B.md_batch(codes, B.md_options_init(work_budget=10 ** 9, autotune=1, tune_cache=cache.encode()))
+    for r in (got, auto):
+        assert r[0] == ref[0] and r[2] == ref[2]
+        assert all(np.array_equal(x, y) for x, y in zip(r[1], ref[1]))
+    checked = 0
+    for (G, n, k), di, wi, si in zip(codes, *ref):
+        if si == B.MD_OK and n <= 80:
+            res = O.bz(G, n, k, threads=8)
+            assert di == res.d and np.array_equal(wi, res.witness), (n, k)
+            checked += 1
+    assert checked >= 10

@@ -273,3 +273,16 @@ def test_tensor_split_heads_are_colex_prefixes(k, g, q, smin):
         assert O.colex_rank(c) == p + tail
         seen.add(c)
     assert len(seen) == math.comb(k, g)                   # (s_min = q when g < q + 2, as planned)
+
+
+def test_batch_tune_key_and_no_gpu(B):
+    """The tuning key names the batch's shape (n and k rounded out, count to a power of two);
+    without a GPU the tuner reports MD_ECUDA rather than guessing."""
+    codes = [(T.pack(T.random_rows(n, k, 40 + i), n), n, k) for i, (n, k) in enumerate([(50, 20), (97, 41), (130, 60)])]
+    assert B.md_batch_tune_key(codes) == "n48-144 k16-64 c2^2"
+    assert B.md_batch_tune_key(codes[:1]) == "n48-64 k16-24 c2^0"
+    import torch
+    if not torch.cuda.is_available():
+        with pytest.raises(B.MDError) as e:
+            B.md_batch_tune(codes)
+        assert e.value.code == B.MD_ECUDA
