@@ -106,7 +106,9 @@ typedef struct md_options {
                                  (tcgen05 MMA over +-1 encodings of the packed rows, exact
                                  integer results); 0 = never; 2 = every level with g >= q + 1
                                  (a test setting).  Results are identical for all. */
-    int tensor_head;          /* head size q of the tensor-core split (2 or 3); 0 = automatic */
+    int tensor_head;          /* head size q of the tensor-core split (2 to 5); 0 = automatic: the
+                                 widest of 5, 4, 3 whose head table (C(k, q) rows of the packed
+                                 width) fits in 1 GiB, else 2 */
     int test_stall;           /* test hook, 0 in normal use.  1 = in every tensor-core level the
                                  tail producers never signal their first tile set, so the
                                  MMA issuers' bounded wait (4 s) runs out: each block frees
@@ -217,7 +219,8 @@ int md_scan_task(md_handle h, int g, int j, int M, uint64_t u0, uint64_t u1, int
 /* The work decomposition of level (g, j) that md_compute uses under the handle's options
    (host-only, no device work).  *kind: 0 = per-lane colex rank ranges (small levels), 2 or
    3 = the head size P of the split enumeration, 4 = the tensor-core product (heads of q
-   elements, q = md_options.tensor_head or 3, and for small c_{q+1} of q + 1 elements).
+   elements, q = md_options.tensor_head or the automatic choice, and for small c_{q+1} of q + 1
+   elements).
    For kind 2/3 each entry i describes the tasks with c_{P+1} = M: tasks[i] = {M, number
    of upper parts, upper parts per lane, first work item}; *count receives the number of
    entries (at most max written); for kinds 0 and 4, *count = 0.  *work_items receives the

@@ -385,7 +385,7 @@ LevelPlan plan_level(const Code &c, int g, int j, const PlanOptions &o) {
         const int q = o.tensor_head ? o.tensor_head : tc_auto_head(k, gm.W);
         const int v = g - q - 1;
         bool use = false;
-        if ((q == 2 || q == 3) && q < k && v >= 0 && v <= tc_max_upper())
+        if (q >= 2 && q <= 5 && q < k && v >= 0 && v <= tc_max_upper())
             use = o.tensor == 2 || (v >= 1 && p.count >= (1ull << 28));
         if (use) {
             p.kind = KIND_TC;

@@ -1027,10 +1027,18 @@ size_t tc_tables_bytes(int k, int q, int W) { return head_bytes(k, q, W); }
 
 size_t tc_heads_bytes(uint64_t nheads, int W) { return (size_t)((nheads + kTcN - 1) / kTcN) * kTcN * 32 * W; }
 
+#ifndef MD_TC_HEAD_TABLE_MAX
+#define MD_TC_HEAD_TABLE_MAX (size_t(1) << 30)
+#endif
 int tc_auto_head(int k, int W) {
-    // three-element heads keep the head dimension of the product wide for every s that
-    // carries much work; fall back to pairs when their table would be too large
-    return (k >= 4 && head_bytes(k, 3, W) <= (size_t(1) << 30)) ? 3 : 2;
+    // The head dimension of a product is C(s, q) for the tail's smallest element s, and s is
+    // small for most combinations when g is a sizeable fraction of k (about q k / g): wider heads
+    // give each tail tile more slices to be multiplied with.  The widest of 5, 4, 3 elements
+    // whose table fits in 1 GiB (k = 100: q = 4, 1.05x over q = 3 on stage 10; k = 56..64:
+    // q = 5, 1.4-2.2x on stages 11-13), pairs beyond.
+    for (int q = 5; q >= 3; q--)
+        if (k > q + 1 && head_bytes(k, q, W) <= MD_TC_HEAD_TABLE_MAX) return q;
+    return 2;
 }
 
 int tc_max_upper() { return kMaxV; }

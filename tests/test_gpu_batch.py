@@ -114,7 +114,7 @@ def test_batch_heavy_codes_run_alone(B, heavy):
     after the shared schedule of the others; every result equals the oracle's, whichever
     route each code takes (2^12: most codes alone; 2^20: a mix; 2^64 - 1: none)."""
     codes = mixed_codes()
-    d, wits, st = B.md_batch(codes, B.md_options_init(batch_heavy=heavy, tensor=2))
+    d, wits, st = B.md_batch(codes, B.md_options_init(batch_heavy=heavy, tensor=2, tensor_head=3))
     assert st == [B.MD_OK] * len(codes)
     for (G, n, k), di, wi in zip(codes, d, wits):
         res = O.bz(G, n, k, threads=8)

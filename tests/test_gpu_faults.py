@@ -144,7 +144,7 @@ def test_caller_allocator_serves_every_buffer(B):
     G, n, k = I.single_code("rand64x32")
     res = O.bz(G, n, k)
     A = TorchAllocator()
-    h = B.md_create(G, n, k, A.options(B, tensor=2))
+    h = B.md_create(G, n, k, A.options(B, tensor=2, tensor_head=3))
     try:
         d, wit = B.md_compute(h, n)
         assert A.calls >= 1 and A.live

@@ -73,7 +73,7 @@ CASES = [(40, 12, 31), (64, 24, 32), (90, 30, 33), (120, 40, 34), (160, 24, 35),
 
 
 @pytest.mark.parametrize("n,k,seed", CASES)
-@pytest.mark.parametrize("q", [2, 3])
+@pytest.mark.parametrize("q", [2, 3, 4, 5])
 def test_forced_tensor_levels(B, n, k, seed, q):
     G = T.pack(T.random_rows(n, k, seed), n)
     res = oracle_cached(G, n, k, (n, k, seed))
@@ -96,7 +96,7 @@ def test_forced_tensor_product_words(B, n, k, seed, filt):
 def test_forced_tensor_per_matrix_rule(B, n, k, seed):
     G = T.pack(T.random_rows(n, k, seed), n)
     res = oracle_cached(G, n, k, (n, k, seed), stop_rule=1)
-    assert_parity(B, G, n, k, res, tensor=2, stop_rule=1)
+    assert_parity(B, G, n, k, res, tensor=2, tensor_head=3, stop_rule=1)
 
 
 @pytest.mark.parametrize("name", sorted(T.TEXTBOOK))
@@ -105,7 +105,7 @@ def test_forced_tensor_textbook(B, name):
     rows, n, k = ctor()
     G = T.pack(rows, n)
     res = O.bz(G, n, k, threads=THREADS)
-    assert_parity(B, G, n, k, res, tensor=2)
+    assert_parity(B, G, n, k, res, tensor=2, tensor_head=3)
     assert res.d == d
 
 
@@ -216,7 +216,7 @@ def test_tensor_mid_level_stop(B):
     the result stays exact."""
     G = T.pack(T.random_rows(100, 33, 41), 100)
     res = oracle_cached(G, 100, 33, (100, 33, 41))
-    info = assert_parity(B, G, 100, 33, res, tensor=2)
+    info = assert_parity(B, G, 100, 33, res, tensor=2, tensor_head=3)
     assert info["skipped_work"] >= 0
 
 
@@ -227,11 +227,11 @@ def test_tensor_wait_timeout_is_reported(B):
     usable and the next run is exact."""
     G, n, k = I.single_code("rand64x32")
     res = oracle_cached(G, n, k, "rand64x32")
-    h = B.md_create(G, n, k, B.md_options_init(tensor=2, test_stall=1))
+    h = B.md_create(G, n, k, B.md_options_init(tensor=2, tensor_head=3, test_stall=1))
     try:
         with pytest.raises(B.MDError) as e:
             B.md_compute(h, n)
         assert e.value.code == 8                       # MD_ETIMEOUT
     finally:
         B.md_destroy(h)
-    assert_parity(B, G, n, k, res, tensor=2)
+    assert_parity(B, G, n, k, res, tensor=2, tensor_head=3)

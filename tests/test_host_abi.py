@@ -156,9 +156,20 @@ def _tc_items(k, g, q, W):
     return items, cover
 
 
+def _auto_q(k, W):
+    """The automatic head size: the widest of 5, 4, 3 elements whose table (C(k, q) heads
+    in 256-row slices of 32 W bytes) fits in 1 GiB, else 2."""
+    import math
+    for q in (5, 4, 3):
+        if k > q + 1 and -(-math.comb(k, q) // 256) * 256 * 32 * W <= 1 << 30:
+            return q
+    return 2
+
+
 @pytest.mark.parametrize("n,k,g,head,tensor", [(200, 100, 8, 0, 1), (200, 100, 10, 0, 1), (128, 64, 7, 0, 1),
                                                (256, 60, 6, 0, 2), (100, 33, 4, 3, 2), (120, 40, 6, 2, 2),
-                                               (90, 30, 9, 0, 2)])
+                                               (90, 30, 9, 0, 2), (160, 60, 12, 0, 1), (200, 100, 9, 3, 1),
+                                               (150, 60, 13, 4, 1), (120, 50, 9, 5, 2)])
 def test_level_plan_tensor_items(B, n, k, g, head, tensor):
     """Levels md_compute runs on the tensor cores report kind 4; the item count matches the
     two-phase split restated here, and the two phases cover the C(k, g) combinations once."""
@@ -168,8 +179,8 @@ def test_level_plan_tensor_items(B, n, k, g, head, tensor):
         kind, tasks, items = B.md_level_plan(h, g, 0)
     finally:
         B.md_destroy(h)
-    q = head or 3
     W = -(-(n - k) // 32)
+    q = head or _auto_q(k, W)
     want, cover = _tc_items(k, g, q, W)
     assert kind == 4 and tasks == []
     assert items == want
@@ -230,7 +241,7 @@ def test_struct_layouts_match_header(B, tmp_path):
             assert int(got["%s.%s" % (S.__name__, f)]) == getattr(S, f).offset, (S.__name__, f)
 
 
-@pytest.mark.parametrize("n,k,g,tensor,why", [(200, 60, 15, 2, "v = 11 upper elements"),
+@pytest.mark.parametrize("n,k,g,tensor,why", [(200, 60, 17, 2, "v = 11 upper elements (q = 5)"),
                                               (200, 100, 5, 1, "C(100, 5) < 2^28"),
                                               (200, 100, 10, 0, "tensor = 0")])
 def test_level_plan_tensor_fallbacks(B, n, k, g, tensor, why):
