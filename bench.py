@@ -8,7 +8,13 @@ codewords/s = the sum of C(k, g) over the completed levels / device time.  At N 
 full computation to d (time-to-d, ~3.2e14 codewords) also runs once, after the timed steps.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference] [--no-time-to-d]
-    python bench.py --workload batch | --workload serve     (the batched and serving workloads)
+    python bench.py --workload batch | --workload serve     (the batched and serving workloads alone)
+
+At N = 1 the default run also measures, after the timed steps: the same stages on the popcount
+kernels against the POPC peak measured on this GPU ("roofline_popcount"), the batch of 2048
+codes with md_batch_tune's options against the per-code loop ("batch"; and under a 1e10
+combination budget, "batch_budget_1e10"), and the serving trace ("serve"), each with its own
+clock samples.
 
 Under torchrun (N > 1) every rank runs an independent replica of the step on its own GPU
 (the path has no cross-GPU exchange); value = all ranks' codewords / the slowest rank's
@@ -43,6 +49,9 @@ TC_KERNEL_TRAFFIC_BYTES = None
 TC_KERNEL_TRAFFIC_NOTE = ("null: the tensor-core kernel changed after its last ncu capture (19184128 B per "
                           "level g=8 launch: the head-table stream, fixed per launch)")
 FP8_PER_BF16 = 2.0                # nominal dense fp8 / bf16 tensor rate (4.5 / 2.25 PFLOP/s)
+# the input of both arms (seed 3's first R draw is invertible, so no draw is skipped)
+DATA = ("synthetic: random code G=[I_100|R], R i.i.d. Bernoulli(1/2) from SplitMix64 seed 3 "
+        "(the first draw; R is invertible)")
 
 
 def parse():
@@ -59,6 +68,10 @@ def parse():
     ap.add_argument("--no-time-to-d", action="store_true",
                     help="skip the full computation to d (run once on rank 0 at N=1 by default)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5, help="steps of the end-to-end leg (at most --steps)")
+    ap.add_argument("--no-popcount", action="store_true", help="skip the popcount-kernel roofline run")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batch lines (all 2048 codes, and under 1e10)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving line")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--verbose", action="store_true", help="per-level records on stderr")
@@ -130,6 +143,16 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def gpu_index() -> int:
+    """The GPU this process uses, as nvidia-smi numbers it."""
+    _, _, local = dist_env()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    parts = vis.split(",")
+    if vis and local < len(parts) and parts[local].strip().isdigit():
+        return int(parts[local])
+    return local
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -193,15 +216,23 @@ def roofline_line(args, n, k, top_g, nlaunch, per_launch_cw, per_launch_s, words
         if burst:
             line["frac_of_burst"] = achieved / (burst * FP8_PER_BF16)
         return line
-    peak = POPC_PER_SM_PER_CLK * NOMINAL_SMS * NOMINAL_MAX_MHZ * 1e6 / 1e9       # Gpopc/s
-    achieved = per_launch_cw * 1.0 / per_launch_s / 1e9                              # 1 popc per codeword (filtered)
+    return popc_roofline(POPC_PER_SM_PER_CLK, NOMINAL_SMS, NOMINAL_MAX_MHZ, top_g, nlaunch, per_launch_cw,
+                         per_launch_s, "16 popc/clk/SM (an earlier probe) x 152 SMs x 2070 MHz max clock")
+
+
+def popc_roofline(per_sm_clk, sms, mhz, top_g, nlaunch, per_launch_cw, per_launch_s, basis):
+    """Roofline of the popcount kernels (the split kernel of the deepest stage): one POPC per
+    codeword (the popcount of the OR of the fewest packed words that bounds the weight; exact
+    weights only for the rare codeword that can reach U) against the POPC pipe's peak."""
+    peak = per_sm_clk * sms * mhz * 1e6 / 1e9                                        # Gpopc/s
+    achieved = per_launch_cw / per_launch_s / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpopc/s", "frac": achieved / peak,
             "traffic": None,
-            "traffic_note": "null: the split kernel changed (per-head U prefetch for the mid-level check) "
-                            "after its ncu capture, which measured %d B per level g=8 launch, a fixed "
+            "traffic_note": "null: the split kernel changed (per-head U prefetch for the mid-level check, cancel "
+                            "polling) after its ncu capture, which measured %d B per level g=8 launch, a fixed "
                             "staging cost that does not grow with codewords" % SPLIT_KERNEL_TRAFFIC_BYTES,
             "kernel": "split_kernel (stage g=%d levels, %d launches timed)" % (top_g, nlaunch),
-            "peak_basis": "16 popc/clk/SM (measured) x 152 SMs x 2070 MHz max clock",
+            "peak_basis": basis,
             "work_basis": "1 popc per codeword: popcount of the OR of the packed words, exact weight "
                           "only for codewords that can reach U"}
 
@@ -256,7 +287,7 @@ def run_reference(args):
         "impl": "reference", "metric": "codewords/s", "value": value, "unit": "codewords/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / len(rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": "synthetic: random code G=[I_k|R], R from SplitMix64 seed (first invertible draw)",
+        "data": DATA,
         "config": workload_config(args, n, k),
         "cpu_baseline": {"value": value, "unit": "codewords/s", "cores": threads, "kind": "oracle",
                          "sample": "colex-rank prefix of level (g=%d, Gamma_1), %d combinations per step"
@@ -302,8 +333,7 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    sampler = ClockSampler(int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0])
-                           if os.environ.get("CUDA_VISIBLE_DEVICES", "").isdigit() else local)
+    sampler = ClockSampler(gpu_index())
     sampler.start()
     ev = []
     infos = []
@@ -342,7 +372,7 @@ def run_ours(args):
         "metric": "codewords/s", "value": value, "unit": "codewords/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic: random code G=[I_100|R], R i.i.d. Bernoulli(1/2) from SplitMix64 seed 3",
+        "data": DATA,
         "config": dict(workload_config(args, n, k), codewords_per_step=infos[0]["codewords"],
                        parallelism="replicas" if ws > 1 else "single GPU"),
         "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
@@ -353,7 +383,8 @@ def run_ours(args):
         # end to end through the C ABI from host buffers: create (host G), compute, destroy
         opt_e = B.md_options_init(max_stage=args.max_stage, filter=args.filter, tensor=args.tensor)
         times, h2d, d2h, cwe = [], 0, 0, 0
-        for _ in range(args.steps):
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        for _ in range(e2e_steps):
             t0 = time.perf_counter()
             hh = B.md_create(G, n, k, opt_e)
             B.md_compute(hh, n)
@@ -363,8 +394,8 @@ def run_ours(args):
             h2d += inf["h2d_bytes"] + G.nbytes
             d2h += inf["d2h_bytes"]
             cwe += inf["codewords"]
-        line["e2e"] = {"value": cwe / sum(times), "unit": "codewords/s",
-                       "h2d_bytes_per_step": h2d // args.steps, "d2h_bytes_per_step": d2h // args.steps}
+        line["e2e"] = {"value": cwe / sum(times), "unit": "codewords/s", "steps": e2e_steps,
+                       "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps}
 
     if rank == 0 and ws == 1 and not args.no_cpu:
         threads = os.cpu_count() or 1
@@ -390,6 +421,44 @@ def run_ours(args):
                              "codewords": inf["codewords"], "stop_stage": inf["stop_g"],
                              "complete": inf["complete"]}
 
+    if rank == 0 and ws == 1 and args.tensor and not args.no_popcount and args.workload == "rand200x100":
+        # the popcount kernels on the same workload (md_options.tensor = 0), against the POPC
+        # peak measured on this GPU: its rate per SM and clock x SMs x the SM clock
+        per_sm_clk = B.md_popc_rate()
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        sampler = ClockSampler(gpu_index())
+        sampler.start()
+        hp = B.md_create(G, n, k, B.md_options_init(max_stage=args.max_stage, filter=args.filter, tensor=0,
+                                                    stream=stream.cuda_stream))
+        B.md_compute(hp, n)
+        info_p = B.md_info_get(hp)
+        lev_p = B.md_levels(hp, with_time=True)
+        B.md_destroy(hp)
+        clocks_p = sampler.stop()
+        gtop = max(lv[0] for lv in lev_p)
+        top_p = [lv for lv in lev_p if lv[0] == gtop]
+        mhz = clocks_p.get("sm_max_mhz") or measured_peaks().get("sm_max_mhz") or NOMINAL_MAX_MHZ
+        rp = popc_roofline(per_sm_clk, sms, mhz, gtop, len(top_p), sum(lv[4] for lv in top_p) / len(top_p),
+                           sum(lv[5] for lv in top_p) / len(top_p),
+                           "md_popc_rate on this GPU: %.2f popc/clk/SM x %d SMs x %.0f MHz max SM clock"
+                           % (per_sm_clk, sms, mhz))
+        rp.update({"popc_per_sm_per_clk": per_sm_clk, "codewords_per_s": info_p["codewords"] / info_p["seconds_device"],
+                   "clocks": clocks_p, "run": "md_compute with tensor = 0, stages g <= %d" % args.max_stage})
+        line["roofline_popcount"] = rp
+
+    if rank == 0 and ws == 1 and not args.no_batch:
+        import tempfile
+        cache = os.path.join(tempfile.gettempdir(), "md_tune_bench_%d.json" % os.getpid())
+        try:
+            line["batch"] = batch_measure(args, B, inputs, 0, cache)
+            line["batch_budget_1e10"] = batch_measure(args, B, inputs, int(1e10), cache)
+        finally:
+            if os.path.exists(cache):
+                os.remove(cache)
+
+    if rank == 0 and ws == 1 and not args.no_serve:
+        line["serve"] = serve_measure(args, B, inputs)
+
     if args.verbose and rank == 0:
         for lv in lev_all[0]:
             sys.stderr.write("level g=%d j=%d weight=%d rank=%d count=%d kernel=%.4f s  %.3e cw/s\n"
@@ -402,27 +471,29 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
-    """Uneven batch (seed 4): one md_batch schedule vs one md_compute per code, same stream."""
+def batch_measure(args, B, inputs, budget, tune_cache=None):
+    """The uneven batch (seed 4): md_batch with options picked by md_batch_tune against one
+    md_compute per code (the per-code launch loop), same GPU and stream, clocks sampled over
+    both.  budget = per-code estimated work limit (0 = every code)."""
     import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_1911_08963_gb300 import binding as B
-    from paper_1911_08963_gb300 import inputs
     codes = inputs.batch_codes(count=args.batch_count)
-    budget = int(args.batch_budget)
-    opt = B.md_options_init(work_budget=budget, chunk_log2=args.chunk_log2)
-    opt_loop = B.md_options_init(work_budget=budget, batch_mode=1, chunk_log2=args.chunk_log2)
+    base = B.md_options_init(work_budget=budget)
+    t0 = time.perf_counter()
+    opt = B.md_batch_tune(codes, base, tune_cache)
+    t_tune = time.perf_counter() - t0
+    opt_loop = B.md_options_init(work_budget=budget, batch_mode=1)
     B.md_batch(codes[:64], opt)                    # warm-up (module load, first allocations)
     B.md_batch(codes[:64], opt_loop)
     torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_index())
+    sampler.start()
     t0 = time.perf_counter()
     d_b, w_b, st_b = B.md_batch(codes, opt)
     t_batch = time.perf_counter() - t0
     t0 = time.perf_counter()
     d_l, w_l, st_l = B.md_batch(codes, opt_loop)
     t_loop = time.perf_counter() - t0
+    clocks = sampler.stop()
     same = d_b == d_l and st_b == st_l and all((x == y).all() for x, y in zip(w_b, w_l))
     done = sum(1 for s_ in st_b if s_ == B.MD_OK)
     skipped = sum(1 for s_ in st_b if s_ == B.MD_EBUDGET)
@@ -431,24 +502,19 @@ def run_batch(args):
         key = "n%d-%d" % (n // 25 * 25, n // 25 * 25 + 24)
         h = hist.setdefault(key, [0, 0])
         h[0 if s_ == B.MD_OK else 1] += 1
-    line = {"metric": "codes/s (batched vs per-code loop)", "value": done / t_batch, "unit": "codes/s",
+    return {"metric": "codes/s (batched vs per-code loop)", "value": done / t_batch, "unit": "codes/s",
             "per_code_loop": done / t_loop, "speedup": t_loop / t_batch, "codes": len(codes), "completed": done,
             "skipped_over_budget": skipped, "seconds_batched": t_batch, "seconds_loop": t_loop,
-            "identical_results": same, "higher_is_better": True, "n_gpus": 1,
-            "config": {"workload": "2048 random codes, seed 4, n~U{48..160}, k~U{n/3..n/2}",
+            "identical_results": same, "higher_is_better": True, "n_gpus": 1, "clocks": clocks,
+            "tuned": {"chunk_log2": opt.chunk_log2, "blocks_per_sm": opt.blocks_per_sm,
+                      "batch_heavy": opt.batch_heavy, "seconds": t_tune},
+            "config": {"workload": "%d random codes, seed 4, n~U{48..160}, k~U{n/3..n/2}" % len(codes),
                        "work_budget": budget, "histogram_done_skipped_by_n": hist}}
-    print(json.dumps(line), flush=True)
-    return 0
 
 
-def run_serve(args):
-    """Poisson stream (seed 5, 200 requests/s) through the continuous-batching server."""
-    import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_1911_08963_gb300 import binding as B
-    from paper_1911_08963_gb300 import inputs
+def serve_measure(args, B, inputs):
+    """Poisson stream (seed 5, 200 requests/s) through the continuous-batching server; requests
+    whose estimated work exceeds the budget are refused at submission (admission by work)."""
     trace = inputs.serving_trace(args.serve_count)
     s = B.md_server_create(slots=args.serve_slots, work_budget=int(args.serve_budget))
     # warm-up: a few small codes through the server
@@ -463,8 +529,10 @@ def run_serve(args):
     lat = []
     rejected = 0
     lock = threading.Lock()
-    start = time.perf_counter()
     stop = [False]
+    sampler = ClockSampler(gpu_index())
+    sampler.start()
+    start = time.perf_counter()
 
     def poller():
         while not stop[0] or outstanding:
@@ -496,16 +564,38 @@ def run_serve(args):
     stop[0] = True
     th.join()
     makespan = time.perf_counter() - start
+    clocks = sampler.stop()
     B.md_server_destroy(s)
     ok = sorted(x for x, st in lat if st == B.MD_OK)
     p = lambda q: ok[min(len(ok) - 1, int(q * len(ok)))] if ok else None
-    line = {"metric": "serving latency p50/p99 and codes/s", "value": len(ok) / makespan, "unit": "codes/s",
+    return {"metric": "serving latency p50/p99 and codes/s", "value": len(ok) / makespan, "unit": "codes/s",
             "p50_ms": p(0.50) * 1e3 if ok else None, "p99_ms": p(0.99) * 1e3 if ok else None,
             "completed": len(ok), "rejected_over_budget": rejected, "requests": len(trace),
             "makespan_s": makespan, "trace_s": trace[-1][0], "higher_is_better": True, "n_gpus": 1,
+            "clocks": clocks,
             "config": {"workload": "Poisson arrivals 200/s, seed 5, n~U{64..200}, k=n/2+U{-8..8}",
                        "work_budget": int(args.serve_budget), "slots": args.serve_slots}}
-    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1911_08963_gb300 import binding as B
+    from paper_1911_08963_gb300 import inputs
+    print(json.dumps(batch_measure(args, B, inputs, int(args.batch_budget))), flush=True)
+    return 0
+
+
+def run_serve(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1911_08963_gb300 import binding as B
+    from paper_1911_08963_gb300 import inputs
+    print(json.dumps(serve_measure(args, B, inputs)), flush=True)
     return 0
 
 

@@ -238,6 +238,12 @@ int md_level_plan(md_handle h, int g, int j, int *kind, md_task_info *tasks, int
 
 void md_destroy(md_handle h);
 
+/* Measurement utility (no counterpart in the paper): the POPC throughput of the current GPU in
+   popc lane-operations per SM per clock, from a kernel whose 16 independent popc/add chains
+   per thread keep the POPC pipe the limit (one block of 1024 threads per SM, clock64 cycles,
+   median over SMs).  The popcount kernels' roofline is this rate x SMs x the SM clock. */
+int md_popc_rate(double *per_sm_per_clk);
+
 /* Static text for a status code. */
 const char *md_strerror(int code);
 
@@ -300,11 +306,12 @@ int md_batch(const md_code *codes, int count, const md_options *opt,
  * the current GPU: the combinations per work item (chunk_log2 in {16, 18, 20}), the blocks per
  * SM of the shared rounds ({occupancy, 2, 4}), and the single-code threshold (batch_heavy in
  * {2^30, 2^32, ..., 2^38}).  It times md_batch on deterministic samples of the batch (every
- * i-th code): up to 384 codes of estimated work below 2^34 for the first two, then up to 24
- * codes between 2^30 and 2^38 for the threshold, and writes into *tuned a copy of *base
- * (defaults if NULL) with the fastest values.  With cache_path, the choice is stored in that
- * JSON file under the key md_batch_tune_key(...) + " | " + the GPU's name, and a later call
- * with the same key reads it back without timing anything.  Codes over base->work_budget
+ * i-th code): up to 384 codes of estimated work below 2^34 for the first two, then those
+ * together with up to 24 codes between 2^30 and 2^38 for the threshold, and writes into *tuned
+ * a copy of *base (defaults if NULL) with the fastest values.  With cache_path, the choice is
+ * stored in that JSON file under the key md_batch_tune_key(...) + " | budget " + the work
+ * budget + " | " + the GPU's name, and a later call with the same key reads it back without
+ * timing anything.  Codes over base->work_budget
  * are left out of the samples.  Returns MD_OK, MD_EINVAL (bad arguments, unwritable cache),
  * MD_ECUDA (no GPU) or the error of a timing run.  The paper's own tuning is the choice of
  * prefix size and threads per process (Section 4); these knobs are this library's analogue.

@@ -87,6 +87,7 @@ PROTOTYPES = {
     "md_scan_range_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ip,
                                              u64p]),
+    "md_popc_rate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "md_destroy": (None, [ctypes.c_void_p]),
     "md_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "md_batch": (ctypes.c_int, [ctypes.POINTER(md_code), ctypes.c_int, ctypes.POINTER(md_options), ip, u64p, ip]),
@@ -216,6 +217,13 @@ def md_scan_range_noalloc(rows_ptr: int, k: int, words: int, weight_base: int, g
     _check(lib.md_scan_range_noalloc(rows_ptr, k, words, weight_base, g, r0, r1, bound, stream, ctypes.byref(w),
                                      ctypes.byref(r)), "md_scan_range_noalloc")
     return w.value, r.value
+
+
+def md_popc_rate() -> float:
+    """POPC lane-operations per SM per clock on the current GPU (include/md.h)."""
+    r = ctypes.c_double()
+    _check(lib.md_popc_rate(ctypes.byref(r)), "md_popc_rate")
+    return r.value
 
 
 def md_destroy(h: int) -> None:

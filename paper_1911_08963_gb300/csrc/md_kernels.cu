@@ -24,7 +24,9 @@
 //     paper's D-* family, Section 3.2, at warp granularity).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "md_device.cuh"
 #include "md_internal.h"
@@ -267,6 +269,31 @@ int level_blocks_per_sm(int kind, int W, bool h2s, int threads, size_t smem) {
     return e == cudaSuccess ? nb : 0;
 }
 
+// ------------------------------------------------------------- POPC throughput ----
+// Every thread runs 16 independent popc -> add chains whose inputs change each iteration (one
+// integer add feeds each popc), so the POPC pipe is the limit: 16 x 32 popc lane-operations per
+// warp iteration against 2 x 16 x 32 integer adds.  One block per SM (the shared-memory request
+// keeps a second one away); cycles by clock64 between two block barriers.
+__global__ void __launch_bounds__(1024, 1) popc_probe_kernel(unsigned iters, unsigned seed, unsigned long long *cycles,
+                                                            unsigned *sink) {
+    uint32_t x[16], acc[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int j = 0; j < 16; j++) x[j] = seed * (threadIdx.x + 1u) + (uint32_t)j * 0x9E3779B9u;
+    __syncthreads();
+    const long long t0 = clock64();
+    for (unsigned i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            x[j] += i;
+            acc[j & 3] += (uint32_t)__popc(x[j]);
+        }
+    }
+    __syncthreads();
+    const long long t1 = clock64();
+    if (threadIdx.x == 0) cycles[blockIdx.x] = (unsigned long long)(t1 - t0);
+    if ((acc[0] ^ acc[1] ^ acc[2] ^ acc[3]) == 0x9E3779B9u) sink[0] = 1u;   // keeps the work live
+}
+
 int max_smem_per_block() {
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
@@ -282,3 +309,38 @@ int sm_count() {
 }
 
 }  // namespace mdl
+
+// POPC lane-operations per SM per clock (median over one block per SM).
+extern "C" int md_popc_rate(double *per_sm_per_clk) {
+    using namespace mdl;
+    if (!per_sm_per_clk) return MD_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1) {
+        cudaGetLastError();
+        return MD_ECUDA;
+    }
+    const int smem = 120 * 1024;
+    unsigned long long *cyc = nullptr;
+    unsigned *sink = nullptr;
+    if (cudaFuncSetAttribute(popc_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaMalloc(&cyc, sizeof(unsigned long long) * sms) != cudaSuccess || cudaMalloc(&sink, 4) != cudaSuccess) {
+        cudaGetLastError();
+        if (cyc) cudaFree(cyc);
+        return MD_ECUDA;
+    }
+    const unsigned iters = 1u << 14;
+    popc_probe_kernel<<<sms, 1024, smem>>>(256u, 7u, cyc, sink);                 // warm-up
+    popc_probe_kernel<<<sms, 1024, smem>>>(iters, 7u, cyc, sink);
+    std::vector<unsigned long long> h(sms);
+    bool ok = cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+              cudaMemcpy(h.data(), cyc, sizeof(unsigned long long) * sms, cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(cyc);
+    cudaFree(sink);
+    if (!ok) { cudaGetLastError(); return MD_ECUDA; }
+    std::sort(h.begin(), h.end());
+    const double med = (double)h[h.size() / 2];
+    if (med <= 0) return MD_EINTERNAL;
+    *per_sm_per_clk = 1024.0 * iters * 16.0 / med;
+    return MD_OK;
+}

@@ -4,10 +4,10 @@
 // and on the GPU: the combinations per work item (chunk_log2), the blocks per SM of the
 // shared round kernels, and the estimated work from which a code runs on its own with the
 // tensor-core levels (batch_heavy).  The tuner times md_batch itself on deterministic samples
-// of the batch -- the light codes for the first two knobs, the mid-weight codes (the only
-// ones the threshold moves) for the third -- and keeps the fastest choice.  Choices are
-// cached in a small JSON file, one entry per (batch shape, GPU), so a batch of a known shape
-// is not timed again.
+// of the batch -- the light codes for the first two knobs, the light codes together with the
+// mid-weight ones (the codes the threshold moves) for the third -- and keeps the fastest
+// choice.  Choices are cached in a small JSON file, one entry per (batch shape, work budget,
+// GPU), so a batch of a known shape is not timed again.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -161,7 +161,8 @@ extern "C" int md_batch_tune(const md_code *codes, int count, const md_options *
         cudaGetLastError();
         return MD_ECUDA;
     }
-    std::string key = std::string(shape) + " | " + prop.name;
+    std::string key = std::string(shape) + " | budget " + std::to_string((unsigned long long)o.work_budget) + " | " +
+                      prop.name;
     for (char &ch : key)
         if (ch == '"' || ch == '\\') ch = '_';
     std::map<std::string, std::string> cache = read_cache(cache_path);
@@ -195,8 +196,15 @@ extern "C" int md_batch_tune(const md_code *codes, int count, const md_options *
             if (dt < 0) return (int)(-1.0 - dt);
             if (best_t < 0 || dt < best_t) { best_t = dt; best_c = ci; best_b = bi; }
         }
-    // mid-weight codes: where the single-code threshold decides the route
-    const std::vector<md_code> mid = sample(codes, est, std::ldexp(1.0, 30), std::min(budget, std::ldexp(1.0, 38)), 24);
+    // the threshold, on the light sample plus mid-weight codes (the ones it moves): taking a code
+    // out of the shared rounds shortens them only as much as the rest of the mix allows
+    std::vector<md_code> mid = sample(codes, est, std::ldexp(1.0, 30), std::min(budget, std::ldexp(1.0, 38)), 24);
+    std::vector<md_code> mix = light;
+    for (const md_code &c : mid) {
+        bool dup = false;
+        for (const md_code &l : light) dup |= l.G == c.G;
+        if (!dup) mix.push_back(c);
+    }
     const double heavies[] = {std::ldexp(1.0, 30), std::ldexp(1.0, 32), std::ldexp(1.0, 34), std::ldexp(1.0, 36),
                               std::ldexp(1.0, 38)};
     unsigned long long best_h = kBatchHeavyDefault;
@@ -206,7 +214,7 @@ extern "C" int md_batch_tune(const md_code *codes, int count, const md_options *
         t.chunk_log2 = best_c;
         t.blocks_per_sm = best_b;
         t.batch_heavy = (unsigned long long)hv;
-        const double dt = time_batch(mid, t, 1);
+        const double dt = time_batch(mix, t, 1);
         if (dt < 0) return (int)(-1.0 - dt);
         if (best_m < 0 || dt < best_m) { best_m = dt; best_h = (unsigned long long)hv; }
     }
@@ -218,8 +226,8 @@ extern "C" int md_batch_tune(const md_code *codes, int count, const md_options *
         char val[512];
         std::snprintf(val, sizeof(val),
                       "{\"chunk_log2\": %d, \"blocks_per_sm\": %d, \"batch_heavy\": %llu, \"light_sample\": %zu, "
-                      "\"light_seconds\": %.6f, \"mid_sample\": %zu, \"mid_seconds\": %.6f}",
-                      best_c, best_b, best_h, light.size(), best_t, mid.size(), best_m);
+                      "\"light_seconds\": %.6f, \"mix_sample\": %zu, \"mix_seconds\": %.6f}",
+                      best_c, best_b, best_h, light.size(), best_t, mix.size(), best_m);
         cache[key] = val;
         rc = write_cache(cache_path, cache);
         if (rc != MD_OK) return rc;
