@@ -40,14 +40,14 @@ PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 POPC_PER_SM_PER_CLK = 16          # measured on GB300 (popc.b32 throughput per SM per clock)
 NOMINAL_SMS = 152
 NOMINAL_MAX_MHZ = 2070.0
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch (level g=8 of rand200x100) measured
-# with ncu; the split kernel's figure predates its last change, so its roofline reports null
-SPLIT_KERNEL_TRAFFIC_BYTES = 160256 + 700928
-# null until the tensor-core kernel, changed since its last capture (products over fewer words),
-# is captured again
-TC_KERNEL_TRAFFIC_BYTES = None
-TC_KERNEL_TRAFFIC_NOTE = ("null: the tensor-core kernel changed after its last ncu capture (19184128 B per "
-                          "level g=8 launch: the head-table stream, fixed per launch)")
+# dram__bytes_read.sum + dram__bytes_write.sum per launch, from ncu captures of the present kernels
+# (profiles/): the split kernel's level (8, Gamma_0) launch, a fixed staging cost that does not grow
+# with the codewords; the tensor-core kernel's level (10, Gamma_0) launch, the one bench.py times
+# (a one-pass capture of the full-size launch; ncu prints 3 significant digits)
+SPLIT_KERNEL_TRAFFIC_BYTES = 157696 + 732160
+TC_KERNEL_TRAFFIC_BYTES = 6570000000 + 13740000
+TC_KERNEL_TRAFFIC_NOTE = ("dram read + write of the level (10, Gamma_0) launch, ncu (one pass): the head-slice "
+                          "stream of a head table (502 MB per matrix) larger than L2; 0.0004 B per codeword")
 FP8_PER_BF16 = 2.0                # nominal dense fp8 / bf16 tensor rate (4.5 / 2.25 PFLOP/s)
 # the input of both arms (seed 3's first R draw is invertible, so no draw is skipped)
 DATA = ("synthetic: random code G=[I_100|R], R i.i.d. Bernoulli(1/2) from SplitMix64 seed 3 "
@@ -227,10 +227,9 @@ def popc_roofline(per_sm_clk, sms, mhz, top_g, nlaunch, per_launch_cw, per_launc
     peak = per_sm_clk * sms * mhz * 1e6 / 1e9                                        # Gpopc/s
     achieved = per_launch_cw / per_launch_s / 1e9
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Gpopc/s", "frac": achieved / peak,
-            "traffic": None,
-            "traffic_note": "null: the split kernel changed (per-head U prefetch for the mid-level check, cancel "
-                            "polling) after its ncu capture, which measured %d B per level g=8 launch, a fixed "
-                            "staging cost that does not grow with codewords" % SPLIT_KERNEL_TRAFFIC_BYTES,
+            "traffic": SPLIT_KERNEL_TRAFFIC_BYTES,
+            "traffic_note": "dram read + write of the level (8, Gamma_0) launch of the same kernel, ncu: a fixed "
+                            "staging cost (rows, pair table, state atomics) that does not grow with codewords",
             "kernel": "split_kernel (stage g=%d levels, %d launches timed)" % (top_g, nlaunch),
             "peak_basis": basis,
             "work_basis": "1 popc per codeword: popcount of the OR of the packed words, exact weight "

@@ -651,15 +651,19 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                     const unsigned long long local = idx - cum[s];
                     const unsigned long long nb = heads_of(a, ph, s);
                     const unsigned long long nsl = (nb + kTcN - 1) / kTcN;
-                    const unsigned long long ngr = (nsl + kGroup - 1) / kGroup;
-                    const unsigned long long grp = local % ngr, tblock = local / ngr;
+                    // consecutive items share a group of head slices and take successive runs
+                    // of tails: the blocks working at once read the same slices, which then stay
+                    // in L2 even when the whole head table does not fit there
+                    const unsigned long long ntails = C(a, k - 1 - s, a.g - a.q - ph - 1);
+                    const unsigned long long ntb = (ntails + per - 1) / per;
+                    const unsigned long long tblock = local % ntb, grp = local / ntb;
                     it.s = s;
                     it.ph = ph;
                     it.nb = (int)nb;
                     it.sl0 = (int)(grp * kGroup);
                     it.nsl = (int)min((unsigned long long)kGroup, nsl - grp * kGroup);
                     it.t0 = tblock * per;
-                    it.nt = (int)min(per, C(a, k - 1 - s, a.g - a.q - ph - 1) - it.t0);
+                    it.nt = (int)min(per, ntails - it.t0);
                     it.na = (it.nt + kTcM - 1) / kTcM;
                     const int U = (int)*(volatile unsigned int *)&st->U;
                     it.u = U;
