@@ -85,7 +85,7 @@ def _build_locked(force: bool, verbose: bool) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp%d" % os.getpid()
-        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))

@@ -4,8 +4,10 @@
 // levels are queued back to back without host round trips; the host only looks at the
 // stop flag one stage behind the device.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <chrono>
 #include <cstring>
 #include <new>
@@ -417,6 +419,13 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
     const int n = c.n, k = c.k, m = (int)c.gam.size();
     fill_static_info(h);
     h->levels.clear();
+    // NVTX ranges (no-ops unless a profiler is attached): the call, and the enqueue of each level
+    char label[64];
+    std::snprintf(label, sizeof(label), "md_compute [%d,%d]", c.n, c.k);
+    nvtxRangePushA(label);
+    struct RangePop {
+        ~RangePop() { nvtxRangePop(); }
+    } range_pop;
 
     cudaEvent_t ev0 = h->run_ev[0], ev1 = h->run_ev[1];
     using Head = md_ctx::Head;
@@ -450,6 +459,8 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
         for (int j = 0; j < m && !err; j++) {
             const int level = (g - 1) * m + j;
             const LevelPlan &p = h->plans[level];
+            std::snprintf(label, sizeof(label), "level g=%d j=%d %s", p.g, p.j, p.kind == KIND_TC ? "tensor" : "popcount");
+            nvtxRangePushA(label);
             cudaEventRecord(h->lev_ev[nlev_ev], s);
             LevelArgs a;
             if (p.kind == KIND_TC) {
@@ -467,6 +478,7 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
             nlev_ev += 2;
             err |= launch_finalize(a, s) != 0;
             launches += 2;
+            nvtxRangePop();
         }
         Head *hd = h->heads + nstages;
         cudaMemcpyAsync(hd, h->dev.st, sizeof(Head), cudaMemcpyDeviceToHost, s);

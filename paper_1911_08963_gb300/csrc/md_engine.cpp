@@ -1,6 +1,8 @@
 // md_engine.cpp -- host side of the multi-code engine and md_batch.
 #include "md_engine.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <atomic>
 #include <cstring>
@@ -553,6 +555,12 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
     }
     const int nc = (int)ok_codes.size();
     if (nc == 0 && heavy_index.empty()) return MD_OK;
+    // NVTX ranges (no-ops unless a profiler is attached): the batch, its shared rounds and
+    // its single-code runs
+    nvtxRangePushA("md_batch");
+    struct RangePop {
+        ~RangePop() { nvtxRangePop(); }
+    } range_pop;
     cudaStream_t s = (cudaStream_t)o.stream;
     cudaStream_t own = nullptr;
     if (!s) {
@@ -561,6 +569,8 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
     }
     int rc = MD_OK;
     if (nc > 0) {
+        nvtxRangePushA("md_batch shared rounds");
+        RangePop rounds_pop;
         Engine eng;
         eng.set_allocator(o.dev_alloc, o.dev_free, o.alloc_ctx);
         rc = eng.init(nc, s, 0, o.blocks_per_sm);
@@ -602,11 +612,13 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
             }
         }
     }
+    if (!heavy_index.empty()) nvtxRangePushA("md_batch single-code runs");
     for (size_t h = 0; rc == MD_OK && h < heavy_index.size(); h++) {
         const int i = heavy_index[h];
         status[i] = single_code_run(codes[i], o, s, &d[i], witness ? witness + woffs[i] : nullptr);
         if (status[i] == MD_ECUDA || status[i] == MD_ENOMEM) rc = status[i];
     }
+    if (!heavy_index.empty()) nvtxRangePop();
     if (own) cudaStreamDestroy(own);
     return rc;
 }
