@@ -244,6 +244,15 @@ void md_destroy(md_handle h);
    median over SMs).  The popcount kernels' roofline is this rate x SMs x the SM clock. */
 int md_popc_rate(double *per_sm_per_clk);
 
+/* The range-checked build (compiled with -DMD_DEBUG_BOUNDS; paper_1911_08963_gb300.build
+   builds it as libmd_debug.so): every index into the shared-memory rows and pair tables, the
+   binomial tables, the work tables, and the tensor-core kernel's tables, tiles and head slices
+   is checked; an index out of range records the check's site and is replaced by a safe one (no
+   trap, no access out of bounds), and the call that launched the kernel returns MD_EINTERNAL.
+   md_debug_bounds gives the last failing site (0 = none): MD_OK in the range-checked build,
+   MD_EUNSUPPORTED (site 0) in the normal one. */
+int md_debug_bounds(unsigned *site);
+
 /* Static text for a status code. */
 const char *md_strerror(int code);
 

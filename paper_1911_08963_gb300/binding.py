@@ -12,7 +12,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libmd.so")
+# MD_LIBRARY selects another build of the same library (the range-checked libmd_debug.so)
+LIB_PATH = os.environ.get("MD_LIBRARY") or os.path.join(_HERE, "_lib", "libmd.so")
 
 MD_OK, MD_EINVAL, MD_ERANK, MD_EUNSUPPORTED, MD_ENOMEM, MD_ECUDA, MD_EBUDGET, MD_ECANCELED, \
     MD_ETIMEOUT, MD_EBUSY, MD_EINTERNAL = range(11)
@@ -88,6 +89,7 @@ PROTOTYPES = {
                                              ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ip,
                                              u64p]),
     "md_popc_rate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "md_debug_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "md_destroy": (None, [ctypes.c_void_p]),
     "md_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "md_batch": (ctypes.c_int, [ctypes.POINTER(md_code), ctypes.c_int, ctypes.POINTER(md_options), ip, u64p, ip]),
@@ -123,6 +125,10 @@ def md_strerror(code: int) -> str:
 
 def _check(rc, where):
     if rc != MD_OK:
+        if rc == MD_EINTERNAL and hasattr(lib, "md_debug_bounds"):
+            debug, site = md_debug_bounds()
+            if debug and site:
+                where = "%s (range check failed at site %d)" % (where, site)
         raise MDError(rc, where)
 
 
@@ -224,6 +230,13 @@ def md_popc_rate() -> float:
     r = ctypes.c_double()
     _check(lib.md_popc_rate(ctypes.byref(r)), "md_popc_rate")
     return r.value
+
+
+def md_debug_bounds():
+    """(is the range-checked build, last failing check site or 0)."""
+    site = ctypes.c_uint()
+    rc = lib.md_debug_bounds(ctypes.byref(site))
+    return rc == MD_OK, site.value
 
 
 def md_destroy(h: int) -> None:

@@ -1,6 +1,7 @@
 """Build the CUDA library libmd.so in-tree (nvcc, sm_103a only).
 
-    python -m paper_1911_08963_gb300.build
+    python -m paper_1911_08963_gb300.build            # libmd.so
+    python -m paper_1911_08963_gb300.build --debug    # libmd_debug.so, range checks on (-DMD_DEBUG_BOUNDS)
 """
 from __future__ import annotations
 
@@ -17,6 +18,8 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libmd.so")
+DEBUG_OBJDIR = os.path.join(HERE, "_build_debug")
+DEBUG_LIB = os.path.join(LIBDIR, "libmd_debug.so")
 SOURCES = ["md_kernels.cu", "md_engine.cu", "md_host.cpp", "md_capi.cpp", "md_engine.cpp", "md_server.cpp", "md_noalloc.cu",
            "md_tc.cu", "md_tune.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -44,20 +47,24 @@ def _stale(target, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile what is stale, under a file lock (several ranks may call this at once)."""
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile what is stale, under a file lock (several ranks may call this at once).
+    debug: the range-checked library (libmd_debug.so), built from the same sources."""
     import fcntl
-    os.makedirs(OBJDIR, exist_ok=True)
+    os.makedirs(DEBUG_OBJDIR if debug else OBJDIR, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     with open(os.path.join(LIBDIR, ".build.lock"), "w") as lock:
         fcntl.flock(lock, fcntl.LOCK_EX)
         try:
-            return _build_locked(force, verbose)
+            return _build_locked(force, verbose, debug)
         finally:
             fcntl.flock(lock, fcntl.LOCK_UN)
 
 
-def _build_locked(force: bool, verbose: bool) -> str:
+def _build_locked(force: bool, verbose: bool, debug: bool = False) -> str:
+    objdir = DEBUG_OBJDIR if debug else OBJDIR
+    lib = DEBUG_LIB if debug else LIB
+    flags = COMMON + (["-DMD_DEBUG_BOUNDS"] if debug else [])
     cc = nvcc()
     headers = _deps()
     srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
@@ -65,10 +72,10 @@ def _build_locked(force: bool, verbose: bool) -> str:
     jobs = []
     for s in srcs:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(OBJDIR, s + ".o")
+        obj = os.path.join(objdir, s + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + headers):
-            cmd = [cc] + ARCH + COMMON + ["-c", src, "-o", obj]
+            cmd = [cc] + ARCH + flags + ["-c", src, "-o", obj]
             if s.endswith(".cu"):
                 cmd += ["-Xptxas", "-v"] if verbose else []
             jobs.append(cmd)
@@ -83,15 +90,15 @@ def _build_locked(force: bool, verbose: bool) -> str:
     if jobs:
         with ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(run, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + ".tmp%d" % os.getpid()
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + ".tmp%d" % os.getpid()
         cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed: %s\n%s%s" % (" ".join(cmd), r.stdout, r.stderr))
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -329,13 +329,41 @@ LevelArgs level_args(md_ctx *h, const LevelPlan &p, int level, bool h2s) {
     return a;
 }
 
+unsigned g_last_bounds_site = 0;    // the debug build's last failing check site
+
 double seconds_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
 }  // namespace
 
+namespace mdl {
+int bounds_status() {
+    unsigned s[4] = {0u, 0u, 0u, 0u};
+    bounds_site_kernels(&s[0], 1);
+    bounds_site_tc(&s[1], 1);
+    bounds_site_engine(&s[2], 1);
+    bounds_site_noalloc(&s[3], 1);
+    for (unsigned v : s)
+        if (v) {
+            g_last_bounds_site = v;
+            return MD_EINTERNAL;
+        }
+    return MD_OK;
+}
+}  // namespace mdl
+
 extern "C" {
+
+int md_debug_bounds(unsigned *site) {
+    if (!site) return MD_EINVAL;
+    *site = g_last_bounds_site;
+#ifdef MD_DEBUG_BOUNDS
+    return MD_OK;
+#else
+    return MD_EUNSUPPORTED;
+#endif
+}
 
 int md_options_init(md_options *opt) {
     if (!opt) return MD_EINVAL;
@@ -569,6 +597,7 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
     for (int i : comb)
         for (int w = 0; w < c.nw64; w++) wv[w] ^= gm.rows[(size_t)i * c.nw64 + w];
     if (popcount_row(wv.data(), c.nw64) != U) return MD_EINTERNAL;
+    if (bounds_status() != MD_OK) return MD_EINTERNAL;          // the debug build's range checks
     h->info.seconds_total = seconds_since(t0);
     if (status != MD_OK) return status;
     *d = U;
@@ -640,6 +669,7 @@ int md_scan_range(md_handle h, int g, int j, uint64_t r0, uint64_t r1, int bound
     unsigned long long key = kNoKey;
     if (!err) err = cudaMemcpyAsync(&key, &h->dev.st->key[0], 8, cudaMemcpyDeviceToHost, s) != cudaSuccess;
     if (cudaStreamSynchronize(s) != cudaSuccess || err) { cudaGetLastError(); return MD_ECUDA; }
+    if (bounds_status() != MD_OK) return MD_EINTERNAL;
     if (key == kNoKey) { *weight = -1; *first_rank = 0; }
     else { *weight = (int)(key >> kRankBits); *first_rank = key & (kRankLimit - 1); }
     return MD_OK;
@@ -696,6 +726,7 @@ int md_scan_task(md_handle h, int g, int j, int M, uint64_t u0, uint64_t u1, int
     if (cudaStreamSynchronize(s) != cudaSuccess) err = true;
     dev_release(h->opt, dtab);
     if (err) { cudaGetLastError(); return MD_ECUDA; }
+    if (bounds_status() != MD_OK) return MD_EINTERNAL;
     if (key == kNoKey) { *weight = -1; *first_rank = 0; }
     else { *weight = (int)(key >> kRankBits); *first_rank = key & (kRankLimit - 1); }
     return MD_OK;

@@ -20,20 +20,60 @@
 namespace mdl {
 namespace dev {
 
+// ---- range checks of the debug build (-DMD_DEBUG_BOUNDS) ----
+// MD_BOUND(idx, lim, site): in the debug build an index at or past its array's limit records
+// `site` in this file's status word (the first failure wins) and is replaced by 0, so the
+// kernel goes on without touching memory out of bounds; the library then reports
+// MD_EINTERNAL and md_debug_bounds returns the site.  In the normal build it is the index.
+#ifdef MD_DEBUG_BOUNDS
+static __device__ unsigned int md_bounds_word;
+static __device__ __noinline__ void md_bounds_fail(unsigned site) { atomicCAS(&md_bounds_word, 0u, site); }
+template <class I>
+__device__ __forceinline__ I md_bound(I idx, unsigned long long lim, unsigned site) {
+    if ((unsigned long long)idx < lim) return idx;
+    md_bounds_fail(site);
+    return (I)0;
+}
+#define MD_BOUND(idx, lim, site) ::mdl::dev::md_bound((idx), (unsigned long long)(lim), (site))
+// The host side of this file's status word: read it into *site and optionally clear it.
+#define MD_BOUNDS_ACCESSOR(name)                                                                    \
+    int name(unsigned *site, int reset) {                                                           \
+        if (cudaMemcpyFromSymbol(site, ::mdl::dev::md_bounds_word, sizeof(unsigned)) != cudaSuccess) \
+            return -1;                                                                              \
+        const unsigned zero = 0;                                                                    \
+        if (reset && cudaMemcpyToSymbol(::mdl::dev::md_bounds_word, &zero, sizeof(unsigned)) != cudaSuccess) \
+            return -1;                                                                              \
+        return 0;                                                                                   \
+    }
+#else
+#define MD_BOUND(idx, lim, site) (idx)
+#define MD_BOUNDS_ACCESSOR(name)                \
+    int name(unsigned *site, int) {             \
+        *site = 0;                              \
+        return 0;                               \
+    }
+#endif
+// Check sites (the value md_debug_bounds reports).
+enum : unsigned {
+    kSiteSmemRow = 1, kSiteGlobRow = 2, kSiteBinom = 3, kSiteMtab = 4, kSiteTcTable = 5, kSiteTcTile = 6,
+    kSiteTcSlice = 7, kSiteTcBinom = 8, kSiteTcTail = 9, kSiteTcHead = 10, kSiteNoallocBinom = 11
+};
+
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kInf = 0x3fffffff;
 constexpr int kNU = kUppersPerLane;           // upper parts a lane walks against each loaded head
 
 __device__ __forceinline__ unsigned long long binom_d(const unsigned long long *tb, int stride, int a, int b) {
-    return (b < 0 || b > a) ? 0ull : __ldg(tb + (size_t)a * stride + b);
+    return (b < 0 || b > a) ? 0ull : __ldg(tb + MD_BOUND((size_t)a * stride + b, (size_t)stride * stride, kSiteBinom));
 }
 
 // Row sources: packed rows of WP words, W of them used (the rest are zero padding).
 template <int W, int WP>
 struct SmemSrc {           // rows in shared memory, read with explicit ld.shared
     uint32_t base;         // shared-window address of row 0
+    uint32_t n = ~0u;      // rows held (checked in the debug build)
     __device__ __forceinline__ void load(int idx, uint32_t (&r)[W]) const {
-        const uint32_t a = base + (uint32_t)idx * (WP * 4);
+        const uint32_t a = base + (uint32_t)MD_BOUND(idx, n, kSiteSmemRow) * (WP * 4);
         if constexpr (WP == 1) {
             asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r[0]) : "r"(a));
         } else if constexpr (WP == 2) {
@@ -63,8 +103,9 @@ struct SmemSrc {           // rows in shared memory, read with explicit ld.share
 template <int W, int WP>
 struct GlobSrc {           // rows in global memory (read-only path)
     const uint32_t *p;
+    uint32_t n = ~0u;      // rows held (checked in the debug build)
     __device__ __forceinline__ void load(int idx, uint32_t (&r)[W]) const {
-        const uint32_t *q = p + (size_t)idx * WP;
+        const uint32_t *q = p + (size_t)MD_BOUND(idx, n, kSiteGlobRow) * WP;
         if constexpr (WP == 1) {
             r[0] = __ldg(q);
         } else if constexpr (WP == 2) {

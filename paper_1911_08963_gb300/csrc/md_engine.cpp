@@ -620,5 +620,6 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
     }
     if (!heavy_index.empty()) nvtxRangePop();
     if (own) cudaStreamDestroy(own);
+    if (rc == MD_OK && bounds_status() != MD_OK) rc = MD_EINTERNAL;      // the debug build's range checks
     return rc;
 }

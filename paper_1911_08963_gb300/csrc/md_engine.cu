@@ -58,15 +58,15 @@ __global__ void __launch_bounds__(kEngineThreads) engine_round_kernel(const Engi
                          nullptr};
         unsigned int *U = &a.states[slot].U;
         int Usnap = (int)*(volatile unsigned int *)U;
-        const GlobSrc<W, WP> rows{L.rows};
+        const GlobSrc<W, WP> rows{L.rows, (uint32_t)cd.k};
         LaneBest best;
         if (L.kind == KIND_SIMPLE) {
             const unsigned long long r0 = (item * 32ull + (unsigned long long)lane) * L.per_chunk;
             const unsigned long long r1 = min(r0 + L.per_chunk, L.count);
             simple_chunk<W, WP>(c, r0, r1, rows, U, Usnap, best);
         } else {
-            const MEntry e = L.mtab[find_entry(L.mtab, L.n_m, item)];
-            const GlobSrc<W, WP> h2{L.h2};
+            const MEntry e = L.mtab[MD_BOUND(find_entry(L.mtab, L.n_m, item), L.n_m, kSiteMtab)];
+            const GlobSrc<W, WP> h2{L.h2, (uint32_t)(cd.k * (cd.k - 1) / 2)};
             if (L.kind == KIND_SPLIT2) split_chunk<W, WP, 2, kNU>(c, e, item, rows, h2, U, Usnap, best);
             else split_chunk<W, WP, 3, kNU>(c, e, item, rows, h2, U, Usnap, best);
         }
@@ -263,5 +263,7 @@ int launch_h2_build_many(const uint32_t *const *rows, uint32_t *const *h2, const
     h2_many_kernel<<<count, 256, 0, (cudaStream_t)stream>>>(rows, h2, k, WP);
     return (int)cudaGetLastError();
 }
+
+MD_BOUNDS_ACCESSOR(bounds_site_engine)
 
 }  // namespace mdl

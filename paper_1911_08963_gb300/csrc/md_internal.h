@@ -243,4 +243,14 @@ int level_blocks_per_sm(int kind, int W, bool h2_in_smem, int threads, size_t sm
 int max_smem_per_block();
 int sm_count();
 
+// Range checks of the debug build (-DMD_DEBUG_BOUNDS): each CUDA source's first failing check
+// site (0 = none), read and optionally cleared; the normal build reports 0.
+int bounds_site_kernels(unsigned *site, int reset);
+int bounds_site_tc(unsigned *site, int reset);
+int bounds_site_engine(unsigned *site, int reset);
+int bounds_site_noalloc(unsigned *site, int reset);
+// MD_EINTERNAL if a range check of the debug build failed since the last call (clears the
+// sites), else MD_OK; always MD_OK in the normal build.
+int bounds_status();
+
 }  // namespace mdl

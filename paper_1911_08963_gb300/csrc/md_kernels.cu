@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(kThreads, 1) split_kernel(const LevelArgs a) {
     __syncthreads();
 
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
-    const SmemSrc<W, WP> rows{sbase};
+    const SmemSrc<W, WP> rows{sbase, (uint32_t)k};
     const ChunkCtx c{k, a.g, a.v, a.base, a.fmax8, a.binom, k + 1,
                      a.check_stop ? &st->L : nullptr, &st->key[a.level], &st->skipped};
     const int lane = threadIdx.x & 31;
@@ -80,13 +80,13 @@ __global__ void __launch_bounds__(kThreads, 1) split_kernel(const LevelArgs a) {
     for (;;) {
         const unsigned long long chunk = next_item(a, lane);
         if (chunk >= a.nchunks) break;
-        const MEntry e = a.mtab[find_entry(a.mtab, a.n_m, chunk)];
+        const MEntry e = a.mtab[MD_BOUND(find_entry(a.mtab, a.n_m, chunk), a.n_m, kSiteMtab)];
         LaneBest best;
         if constexpr (H2S) {
-            const SmemSrc<W, WP> h2{sbase + (uint32_t)rows_words * 4u};
+            const SmemSrc<W, WP> h2{sbase + (uint32_t)rows_words * 4u, (uint32_t)(k * (k - 1) / 2)};
             split_chunk<W, WP, P, kNU>(c, e, chunk, rows, h2, &st->U, Usnap, best);
         } else {
-            const GlobSrc<W, WP> h2{a.h2};
+            const GlobSrc<W, WP> h2{a.h2, (uint32_t)(k * (k - 1) / 2)};
             split_chunk<W, WP, P, kNU>(c, e, chunk, rows, h2, &st->U, Usnap, best);
         }
         publish(&st->key[a.level], best);
@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(kThreads, 1) simple_kernel(const LevelArgs a) 
     const int k = a.k;
     stage_to_smem(smem, a.rows, k * WP);
     __syncthreads();
-    const SmemSrc<W, WP> rows{(uint32_t)__cvta_generic_to_shared(smem)};
+    const SmemSrc<W, WP> rows{(uint32_t)__cvta_generic_to_shared(smem), (uint32_t)k};
     const ChunkCtx c{k, a.g, a.v, a.base, a.fmax8, a.binom, k + 1,
                      a.check_stop ? &st->L : nullptr, &st->key[a.level], &st->skipped};
     const int lane = threadIdx.x & 31;
@@ -300,6 +300,8 @@ int max_smem_per_block() {
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     return v;
 }
+
+MD_BOUNDS_ACCESSOR(bounds_site_kernels)
 
 int sm_count() {
     int dev = 0, v = 0;

@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kThreads) noalloc_scan_kernel(const uint32_t *
     const unsigned long long *tb = reinterpret_cast<const unsigned long long *>(scratch + kBinomOffset);
     stage_to_smem(smem, rows_g, k * WP);
     __syncthreads();
-    const SmemSrc<W, WP> rows{(uint32_t)__cvta_generic_to_shared(smem)};
+    const SmemSrc<W, WP> rows{(uint32_t)__cvta_generic_to_shared(smem), (uint32_t)k};
     const ChunkCtx c{k, g, 0, base, 0ull, tb, kNoAllocMaxK + 1, nullptr, nullptr, nullptr};
     const int lane = threadIdx.x & 31;
     int Usnap = (int)*(volatile unsigned int *)&st->U;
@@ -109,6 +109,9 @@ int scratch_for_current_device(unsigned char **out) {
 }
 
 }  // namespace
+
+MD_BOUNDS_ACCESSOR(bounds_site_noalloc)
+
 }  // namespace mdl
 
 using namespace mdl;
@@ -160,6 +163,7 @@ extern "C" int md_scan_range_noalloc(const uint32_t *rows, int k, int words, int
     if (e == cudaSuccess) e = cudaMemcpyAsync(&key, &st->key, 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { cudaGetLastError(); return MD_ECUDA; }
+    if (bounds_status() != MD_OK) return MD_EINTERNAL;
     if (key == kNoKey) { *weight = -1; *first_rank = 0; }
     else { *weight = (int)(key >> kRankBits); *first_rank = key & (kRankLimit - 1); }
     return MD_OK;

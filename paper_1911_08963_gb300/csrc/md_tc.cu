@@ -372,7 +372,8 @@ struct TcArgs {
 };
 
 __device__ __forceinline__ unsigned long long C(const TcArgs &a, int n, int r) {
-    return (r < 0 || n < r) ? 0ull : __ldg(a.binom + (size_t)n * (a.k + 1) + r);
+    return (r < 0 || n < r) ? 0ull
+                            : __ldg(a.binom + MD_BOUND((size_t)n * (a.k + 1) + r, (size_t)(a.k + 1) * (a.k + 1), kSiteTcBinom));
 }
 
 // Largest x in [lo, hi] with C(x, i) <= t (C(lo, i) <= t holds).
@@ -397,7 +398,9 @@ __device__ __forceinline__ void tail_unrank(const TcArgs &a, const unsigned long
 #pragma unroll
     for (int i = kMaxV; i >= 1; i--) {
         if (i <= v) {
-            auto Cb = [&](int x) { return bs ? bs[x * (kMaxV + 1) + i] : C(a, x, i); };
+            auto Cb = [&](int x) {
+                return bs ? bs[MD_BOUND(x * (kMaxV + 1) + i, (a.k + 1) * (kMaxV + 1), kSiteTcBinom)] : C(a, x, i);
+            };
             const int lo = i - 1, hi = top;
             int x;
             if (i == 1) {
@@ -451,7 +454,7 @@ template <int NW>
 __device__ __forceinline__ void xor_words(uint32_t (&S)[NW], const uint32_t *tab, int k, int x, int w0, int W) {
 #pragma unroll
     for (int i = 0; i < NW; i++)
-        if (w0 + i < W) S[i] ^= tab[(w0 + i) * k + x];
+        if (w0 + i < W) S[i] ^= tab[(w0 + i) * k + MD_BOUND(x, k, kSiteTcTable)];
 }
 
 // The epilogue's rare path, for a warp in which some row's maximum reached the threshold
@@ -502,8 +505,8 @@ __device__ __noinline__ int tc_publish(const TcArgs a, const uint32_t *rT, const
         tail_unrank(a, bs, s, v, tail, o);
 #pragma unroll
         for (int w = 0; w < W; w++) {
-            S[w] = rT[w * k + s];
-            for (int i = 0; i < v; i++) S[w] ^= rT[w * k + o[i]];
+            S[w] = rT[w * k + MD_BOUND(s, k, kSiteTcTail)];
+            for (int i = 0; i < v; i++) S[w] ^= rT[w * k + MD_BOUND(o[i], k, kSiteTcTail)];
         }
     }
     int bw = 0x7fffffff, bc = -1;
@@ -526,7 +529,7 @@ __device__ __noinline__ int tc_publish(const TcArgs a, const uint32_t *rT, const
                 t -= C(a, x, e);
                 hi = x - 1;
 #pragma unroll
-                for (int w = 0; w < W; w++) H[w] ^= rT[w * k + x];
+                for (int w = 0; w < W; w++) H[w] ^= rT[w * k + MD_BOUND(x, k, kSiteTcHead)];
             }
             int wt = a.base;
 #pragma unroll
@@ -712,7 +715,11 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                 const int buf = (int)(step & 1);
                 const int npad = (slice_heads(it, sl) + 15) & ~15;
                 const uint32_t bytes = (uint32_t)(npad / 8) * Cfg::kSbo;
-                const unsigned char *src = a.heads[it.ph] + (size_t)sl * Cfg::kBTile;
+#ifdef MD_DEBUG_BOUNDS
+                // the table of phase ph holds C(k, q) (ph 0) or C(s_min, q + 1) (ph 1) heads in 256-row slices
+                const unsigned long long nslices = ((it.ph ? C(a, a.smin, a.q + 1) : C(a, k, a.q)) + kTcN - 1) / kTcN;
+#endif
+                const unsigned char *src = a.heads[it.ph] + (size_t)MD_BOUND(sl, nslices, kSiteTcSlice) * Cfg::kBTile;
                 mbar_expect_tx(saddr(&sh.bfull[buf]), bytes);
                 bulk_g2s(saddr(Btile + buf * Cfg::kBTile), src, bytes, saddr(&sh.bfull[buf]));
                 pend_buf = buf;
@@ -833,7 +840,9 @@ __global__ void __maxnreg__(kTcMaxRegs) tc_kernel(const TcArgs a) {
                 for (int m = 0; m < kProdRows * it.na; m++) {
                     const int r = p + (kTcM / kProdRows) * (m / it.na);
                     const int t = m % it.na;
-                    unsigned char *rowp = Atile + (set * T + t) * Cfg::kATile + (r >> 3) * Cfg::kSbo + (r & 7) * 16;
+                    unsigned char *rowp =
+                        Atile + MD_BOUND((set * T + t) * Cfg::kATile + (r >> 3) * Cfg::kSbo + (r & 7) * 16,
+                                         2 * T * Cfg::kATile - (W - 1) * 256 - 143, kSiteTcTile);
                     const bool valid = m < cnt;
 #pragma unroll
                     for (int i = 0; i < NW; i++) {
@@ -1028,6 +1037,8 @@ size_t head_bytes(int k, int q, int W) {
 }  // namespace
 
 size_t tc_tables_bytes(int k, int q, int W) { return head_bytes(k, q, W); }
+
+MD_BOUNDS_ACCESSOR(bounds_site_tc)
 
 size_t tc_heads_bytes(uint64_t nheads, int W) { return (size_t)((nheads + kTcN - 1) / kTcN) * kTcN * 32 * W; }
 
