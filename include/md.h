@@ -189,6 +189,22 @@ int md_create_ex(const uint64_t *G, int n, int k, const md_options *opt, md_hand
    d.  Device buffers are allocated on the first call and reused. */
 int md_compute(md_handle h, int *d, uint64_t *witness);
 
+/* Checkpoint and resume (the paper has no counterpart; a run's state is small: the bounds and
+   one record per level).  md_checkpoint, after an md_compute that stopped early -- cancelled
+   (MD_ECANCELED), over budget (MD_EBUDGET) or at md_options.max_stage -- or that finished,
+   writes that run's state at its last completed level into buf: the bounds L and U (U taken
+   from the completed levels' records, so a level the run did not complete leaves no trace),
+   and each completed level's record.  *size receives the bytes needed; with cap below that,
+   nothing is written and MD_EINVAL is returned (call with buf = NULL to ask for the size).
+   MD_EINVAL also when the handle has run no md_compute.  md_resume loads such a buffer into a
+   handle made from the same G, n, k, stop rule and column-order options (checked; MD_EINVAL
+   otherwise); its next md_compute starts at the level after the checkpoint and returns the d,
+   witness and level records of an uninterrupted run, whatever else the options say (a larger
+   max_stage, another stream, ...).  The buffer is plain bytes, caller-owned, valid across
+   processes on machines of the same byte order. */
+int md_checkpoint(md_handle h, void *buf, size_t cap, size_t *size);
+int md_resume(md_handle h, const void *buf, size_t size);
+
 /* Details of the last md_compute (md_create alone fills n, k, m, ranks). */
 int md_info_get(md_handle h, md_info *info);
 

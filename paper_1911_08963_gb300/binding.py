@@ -76,6 +76,8 @@ PROTOTYPES = {
     "md_create_ex": (ctypes.c_int, [u64p, ctypes.c_int, ctypes.c_int, ctypes.POINTER(md_options),
                                     ctypes.POINTER(ctypes.c_void_p)]),
     "md_compute": (ctypes.c_int, [ctypes.c_void_p, ip, u64p]),
+    "md_checkpoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "md_resume": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t]),
     "md_info_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(md_info)]),
     "md_levels": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(md_level), ctypes.c_int, ip]),
     "md_gamma": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, u64p, ip]),
@@ -163,6 +165,21 @@ def md_compute(h: int, n: int):
     wit = np.zeros((n + 63) // 64, dtype=np.uint64)
     _check(lib.md_compute(h, ctypes.byref(d), wit.ctypes.data_as(u64p)), "md_compute")
     return d.value, wit
+
+
+def md_checkpoint(h: int) -> bytes:
+    """The state of the handle's last md_compute at its last completed level (include/md.h)."""
+    size = ctypes.c_size_t()
+    _check(lib.md_checkpoint(h, None, 0, ctypes.byref(size)), "md_checkpoint")
+    buf = ctypes.create_string_buffer(max(1, size.value))
+    _check(lib.md_checkpoint(h, buf, size.value, ctypes.byref(size)), "md_checkpoint")
+    return buf.raw[:size.value]
+
+
+def md_resume(h: int, ckpt: bytes) -> None:
+    """Arm the handle's next md_compute to continue from a checkpoint."""
+    buf = ctypes.create_string_buffer(ckpt, len(ckpt))
+    _check(lib.md_resume(h, buf, len(ckpt)), "md_resume")
 
 
 def md_info_get(h: int) -> dict:

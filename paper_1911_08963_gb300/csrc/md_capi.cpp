@@ -63,6 +63,8 @@ struct md_ctx {
     uint64_t setup_h2d = 0;
     volatile int *cancel_host = nullptr;    // mapped pinned word the kernels poll per work item
     const volatile int *cancel_dev = nullptr;
+    bool have_state = false;                // host_state holds the end of the last md_compute
+    std::vector<char> resume;               // a checkpoint armed for the next md_compute
 };
 
 namespace {
@@ -335,6 +337,72 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// ---- checkpoints: a header, then the completed levels' records and the U each started with ----
+constexpr uint64_t kCkptMagic = 0x3130545048434B4Dull;     // "MKCHPT01"
+struct CkptHeader {
+    uint64_t magic;
+    uint64_t code_hash;     // the code in processing order and the stop rule (level order and bounds)
+    int32_t n, k, m, nlev;  // nlev = completed levels: 0 .. nlev-1 in (g, j) order
+    uint32_t U;             // least weight among the completed levels' records (n + 1: none)
+    int32_t L;              // lower bound after the last completed level
+    int32_t stop;           // L >= U: the run is complete
+    int32_t pad;
+};                          // then uint64 key[nlev], uint32 u_in[nlev]
+
+uint64_t code_hash(const md_ctx *h) {
+    uint64_t x = 1469598103934665603ull;
+    auto mix = [&](const void *p, size_t bytes) {
+        for (size_t i = 0; i < bytes; i++) x = (x ^ ((const unsigned char *)p)[i]) * 1099511628211ull;
+    };
+    const Code &c = h->code;
+    mix(&c.n, sizeof(c.n));
+    mix(&c.k, sizeof(c.k));
+    mix(&h->opt.stop_rule, sizeof(h->opt.stop_rule));
+    mix(c.G.data(), c.G.size() * sizeof(uint64_t));
+    mix(c.perm.data(), c.perm.size() * sizeof(int));
+    return x;
+}
+
+// Validate a checkpoint image against the handle; MD_OK with *hdr filled.
+int parse_checkpoint(const md_ctx *h, const void *buf, size_t size, CkptHeader *hdr) {
+    if (!buf || size < sizeof(CkptHeader)) return MD_EINVAL;
+    std::memcpy(hdr, buf, sizeof(CkptHeader));
+    const int m = (int)h->code.gam.size();
+    if (hdr->magic != kCkptMagic || hdr->code_hash != code_hash(h) || hdr->n != h->code.n || hdr->k != h->code.k ||
+        hdr->m != m || hdr->nlev < 0 || hdr->nlev > std::min(h->code.k * m, kMaxLevels - 1) ||
+        size != sizeof(CkptHeader) + (size_t)hdr->nlev * 12 || hdr->U > (uint32_t)h->code.n + 1)
+        return MD_EINVAL;
+    return MD_OK;
+}
+
+// Queue the device state of a checkpoint on stream s (after the state initialisation).
+int restore_checkpoint(md_ctx *h, const std::vector<char> &img, cudaStream_t s, int *first_level) {
+    CkptHeader hdr;
+    if (parse_checkpoint(h, img.data(), img.size(), &hdr) != MD_OK) return MD_EINVAL;
+    std::vector<unsigned char> raw(sizeof(DevState));
+    DevState &st = *reinterpret_cast<DevState *>(raw.data());
+    st.U = hdr.U;
+    st.L = hdr.L;
+    st.stop = hdr.stop;
+    st.error = 0;
+    st.last_level = hdr.nlev - 1;
+    st.pad = 0;
+    st.skipped = 0;
+    const unsigned long long *keys = reinterpret_cast<const unsigned long long *>(img.data() + sizeof(CkptHeader));
+    const uint32_t *u_in = reinterpret_cast<const uint32_t *>(img.data() + sizeof(CkptHeader) + (size_t)hdr.nlev * 8);
+    for (int i = 0; i < kMaxLevels; i++) {
+        st.key[i] = i < hdr.nlev ? keys[i] : kNoKey;
+        st.u_in[i] = i < hdr.nlev ? u_in[i] : hdr.U;
+        st.ctr[i] = 0;
+    }
+    if (cudaMemcpyAsync(h->dev.st, raw.data(), raw.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return MD_ECUDA;
+    }
+    *first_level = hdr.nlev;
+    return MD_OK;
+}
+
 }  // namespace
 
 namespace mdl {
@@ -363,6 +431,45 @@ int md_debug_bounds(unsigned *site) {
 #else
     return MD_EUNSUPPORTED;
 #endif
+}
+
+int md_checkpoint(md_handle h, void *buf, size_t cap, size_t *size) {
+    if (!h || !size || !h->have_state || !h->host_state) return MD_EINVAL;
+    const DevState &st = *h->host_state;
+    const int n = h->code.n;
+    CkptHeader hdr{};
+    hdr.magic = kCkptMagic;
+    hdr.code_hash = code_hash(h);
+    hdr.n = n;
+    hdr.k = h->code.k;
+    hdr.m = (int)h->code.gam.size();
+    hdr.nlev = st.last_level + 1;
+    // U from the completed levels only: a level cut short by a cancel may have lowered the
+    // device's U with a codeword whose record was not kept
+    unsigned U = (unsigned)n + 1;
+    for (int i = 0; i < hdr.nlev; i++)
+        if (st.key[i] != kNoKey) U = std::min(U, (unsigned)(st.key[i] >> kRankBits));
+    hdr.U = U;
+    hdr.L = st.L;
+    hdr.stop = st.L >= (int)U ? 1 : 0;        // the stop of Alg. 1, whatever ended the run
+    const size_t need = sizeof(CkptHeader) + (size_t)hdr.nlev * 12;
+    *size = need;
+    if (!buf) return MD_OK;
+    if (cap < need) return MD_EINVAL;
+    char *out = (char *)buf;
+    std::memcpy(out, &hdr, sizeof(hdr));
+    std::memcpy(out + sizeof(hdr), st.key, (size_t)hdr.nlev * 8);
+    std::memcpy(out + sizeof(hdr) + (size_t)hdr.nlev * 8, st.u_in, (size_t)hdr.nlev * 4);
+    return MD_OK;
+}
+
+int md_resume(md_handle h, const void *buf, size_t size) {
+    if (!h) return MD_EINVAL;
+    CkptHeader hdr;
+    const int rc = parse_checkpoint(h, buf, size, &hdr);
+    if (rc != MD_OK) return rc;
+    h->resume.assign((const char *)buf, (const char *)buf + size);
+    return MD_OK;
 }
 
 int md_options_init(md_options *opt) {
@@ -463,11 +570,21 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
     uint64_t h2d = 0, d2h = 0;
     bool err = launch_state_init(h->dev.st, (unsigned)(n + 1), s) != 0;
     launches++;
+    // a resumed run: the bounds and the completed levels' records of the checkpoint, and the
+    // stage loop from the level after it
+    int first_level = 0;
+    if (!h->resume.empty()) {
+        std::vector<char> img;
+        img.swap(h->resume);
+        if (!err) err = restore_checkpoint(h, img, s, &first_level) != MD_OK;
+        h2d += img.size();
+    }
     cudaEventRecord(ev0, s);
     uint64_t planned = 0;
     int status = MD_OK;
     bool stopped = false;
-    int g = 1;
+    std::vector<int> ev_level;              // the level timed by each pair of events
+    int g = first_level / m + 1;
     for (; g <= k && !err; g++) {
         if (g > h->g_limit) { status = MD_EUNSUPPORTED; break; }
         if (h->opt.max_stage > 0 && g > h->opt.max_stage) break;
@@ -484,8 +601,9 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
             break;
         }
         planned += stage_work;
-        for (int j = 0; j < m && !err; j++) {
+        for (int j = (g - 1) * m < first_level ? first_level % m : 0; j < m && !err; j++) {
             const int level = (g - 1) * m + j;
+            ev_level.push_back(level);
             const LevelPlan &p = h->plans[level];
             std::snprintf(label, sizeof(label), "level g=%d j=%d %s", p.g, p.j, p.kind == KIND_TC ? "tensor" : "popcount");
             nvtxRangePushA(label);
@@ -523,13 +641,14 @@ int md_compute(md_handle h, int *d, uint64_t *witness) {
     if (wait_event(h, ev1) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) err = true;
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev0, ev1);
-    std::vector<double> lev_sec(nlev_ev / 2, 0.0);
+    std::vector<double> lev_sec((size_t)h->g_limit * m, 0.0);      // per level index (0: not run in this call)
     for (int i = 0; i + 1 < nlev_ev; i += 2) {
         float lms = 0.f;
-        if (cudaEventElapsedTime(&lms, h->lev_ev[i], h->lev_ev[i + 1]) == cudaSuccess) lev_sec[i / 2] = lms * 1e-3;
+        if (cudaEventElapsedTime(&lms, h->lev_ev[i], h->lev_ev[i + 1]) == cudaSuccess) lev_sec[ev_level[i / 2]] = lms * 1e-3;
     }
     if (err) { cudaGetLastError(); return MD_ECUDA; }
     if (cudaMemcpy(h->host_state, h->dev.st, sizeof(DevState), cudaMemcpyDeviceToHost) != cudaSuccess) return MD_ECUDA;
+    h->have_state = true;
     d2h += sizeof(DevState);
     const DevState &st = *h->host_state;
     if (st.error) return st.error == MD_ETIMEOUT || st.error == MD_ECANCELED ? st.error : MD_EINTERNAL;

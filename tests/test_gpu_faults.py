@@ -7,6 +7,9 @@
   * Allocation failure: the caller's device allocator (md_options.dev_alloc) returns NULL, so
     md_compute and md_batch return MD_ENOMEM; a working caller allocator (torch's) serves every
     device buffer, and the results are exact.
+  * Checkpoint and resume: a run cancelled mid-level, or stopped at a stage limit, is
+    checkpointed at its last completed level, resumed in another handle, and gives exactly the
+    uninterrupted run's d, witness and level records.
 """
 import ctypes
 import os
@@ -159,3 +162,71 @@ def test_caller_allocator_serves_every_buffer(B):
         assert sc == B.MD_OK
         r = O.bz(Gc, nc, kc, threads=THREADS)
         assert dc == r.d and np.array_equal(wc, r.witness)
+
+
+def test_resume_after_cancel_equals_uninterrupted(B):
+    """Cancel [200,100] (stages <= 10, tensor cores) one second in, checkpoint, resume in a new
+    handle: the same d, witness and every level record as an uninterrupted run; the checkpoint
+    holds only levels the cancelled run completed."""
+    G, n, k = I.single_code("rand200x100")
+    flag = ctypes.c_int(0)
+    opt = B.md_options_init(max_stage=10)
+    opt.cancel_flag = ctypes.pointer(flag)
+    h = B.md_create(G, n, k, opt)
+    try:
+        timer = threading.Timer(1.0, lambda: setattr(flag, "value", 1))
+        timer.start()
+        with pytest.raises(B.MDError) as e:
+            B.md_compute(h, n)
+        timer.join()
+        assert e.value.code == B.MD_ECANCELED
+        ckpt = B.md_checkpoint(h)
+    finally:
+        B.md_destroy(h)
+    nlev = (len(ckpt) - 48) // 12
+    assert 0 < nlev < 20                          # stopped inside stage 10 (levels 18, 19)
+    d2, wit2, lev2 = levels_of(B, G, n, k, max_stage=10)
+    h = B.md_create(G, n, k, B.md_options_init(max_stage=10))
+    try:
+        B.md_resume(h, ckpt)
+        d, wit = B.md_compute(h, n)
+        lev = B.md_levels(h)
+        info = B.md_info_get(h)
+    finally:
+        B.md_destroy(h)
+    assert d == d2 and np.array_equal(wit, wit2) and lev == lev2
+    assert info["codewords"] == sum(x[4] for x in lev2)
+
+
+def test_resume_extends_a_stage_limited_run(B):
+    """A run stopped at max_stage = 6, resumed with max_stage = 8, equals a max_stage = 8 run;
+    the first stages equal the oracle's records, and a checkpoint of another code is refused."""
+    G, n, k = I.single_code("rand200x100")
+    h = B.md_create(G, n, k, B.md_options_init(max_stage=6))
+    try:
+        B.md_compute(h, n)
+        ckpt = B.md_checkpoint(h)
+    finally:
+        B.md_destroy(h)
+    h = B.md_create(G, n, k, B.md_options_init(max_stage=8))
+    try:
+        B.md_resume(h, ckpt)
+        d, wit = B.md_compute(h, n)
+        lev = B.md_levels(h)
+    finally:
+        B.md_destroy(h)
+    d2, wit2, lev2 = levels_of(B, G, n, k, max_stage=8)
+    assert d == d2 and np.array_equal(wit, wit2) and lev == lev2
+    res = O.bz(G, n, k, threads=THREADS, stop_after_g=5)
+    U = n + 1
+    for got, (g, j, w, first, count) in zip(lev, res.levels):
+        assert tuple(got) == ((g, j, w, first, count) if w <= U else (g, j, -1, 0, count))
+        U = min(U, w)
+    G2, n2, k2 = I.single_code("rand128x64")
+    h = B.md_create(G2, n2, k2)
+    try:
+        with pytest.raises(B.MDError) as e:
+            B.md_resume(h, ckpt)
+        assert e.value.code == B.MD_EINVAL
+    finally:
+        B.md_destroy(h)

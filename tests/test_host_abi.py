@@ -297,3 +297,20 @@ def test_batch_tune_key_and_no_gpu(B):
         with pytest.raises(B.MDError) as e:
             B.md_batch_tune(codes)
         assert e.value.code == B.MD_ECUDA
+
+
+def test_checkpoint_and_resume_reject_what_they_cannot_use(B):
+    """md_checkpoint needs a finished md_compute on the handle; md_resume checks its buffer
+    (size, magic, the code and stop rule it was taken from) and takes nothing else."""
+    n, k = 40, 12
+    h = B.md_create(T.pack(T.random_rows(n, k, 3), n), n, k)
+    try:
+        with pytest.raises(B.MDError) as e:
+            B.md_checkpoint(h)
+        assert e.value.code == B.MD_EINVAL
+        for junk in (b"", b"x" * 7, b"\0" * 48, b"MKCHPT01" + b"\0" * 40, b"\xff" * 200):
+            with pytest.raises(B.MDError) as e:
+                B.md_resume(h, junk)
+            assert e.value.code == B.MD_EINVAL
+    finally:
+        B.md_destroy(h)
