@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--serve-count", type=int, default=2000)
     ap.add_argument("--serve-budget", type=float, default=1e11)
     ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-heavy", type=float, default=0,
+                    help="estimated work from which a request runs alone on the tensor cores "
+                         "(0 = library default 2^30, -1 = never)")
     ap.add_argument("--profile-once", action="store_true",
                     help="one md_compute up to --max-stage and exit (a target for ncu captures)")
     return ap.parse_args()
@@ -515,7 +518,8 @@ def serve_measure(args, B, inputs):
     """Poisson stream (seed 5, 200 requests/s) through the continuous-batching server; requests
     whose estimated work exceeds the budget are refused at submission (admission by work)."""
     trace = inputs.serving_trace(args.serve_count)
-    s = B.md_server_create(slots=args.serve_slots, work_budget=int(args.serve_budget))
+    heavy = 2 ** 64 - 1 if args.serve_heavy < 0 else int(args.serve_heavy)
+    s = B.md_server_create(slots=args.serve_slots, work_budget=int(args.serve_budget), heavy=heavy)
     # warm-up: a few small codes through the server
     for t, G, n, k in trace[:8]:
         try:
@@ -573,7 +577,8 @@ def serve_measure(args, B, inputs):
             "makespan_s": makespan, "trace_s": trace[-1][0], "higher_is_better": True, "n_gpus": 1,
             "clocks": clocks,
             "config": {"workload": "Poisson arrivals 200/s, seed 5, n~U{64..200}, k=n/2+U{-8..8}",
-                       "work_budget": int(args.serve_budget), "slots": args.serve_slots}}
+                       "work_budget": int(args.serve_budget), "slots": args.serve_slots,
+                       "heavy": "never" if args.serve_heavy < 0 else int(args.serve_heavy) or 2 ** 30}}
 
 
 def run_batch(args):

@@ -361,6 +361,12 @@ typedef struct md_server_opts {
     size_t device_bytes;        /* device memory for resident codes (0 = default 256 MiB) */
     void *stream;               /* cudaStream_t or NULL */
     int stop_rule;              /* as md_options.stop_rule */
+    uint64_t heavy;             /* requests whose estimated work reaches this run one at a time
+                                   as single-code computations with the tensor-core levels, on a
+                                   second worker thread and a stream of the server's own (their
+                                   device memory is their own, outside device_bytes), while
+                                   lighter requests share the ticks of the resident slots;
+                                   0 = default 2^30, UINT64_MAX = every request in the slots */
 } md_server_opts;
 
 int md_server_create(const md_server_opts *opts, md_server **out);

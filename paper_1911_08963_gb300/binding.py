@@ -67,7 +67,7 @@ class md_code(ctypes.Structure):
 
 class md_server_opts(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("work_budget", ctypes.c_uint64), ("device_bytes", ctypes.c_size_t),
-                ("stream", ctypes.c_void_p), ("stop_rule", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("stop_rule", ctypes.c_int), ("heavy", ctypes.c_uint64)]
 
 
 PROTOTYPES = {
@@ -306,8 +306,8 @@ def md_batch(codes, options: md_options | None = None):
 
 
 def md_server_create(slots: int = 0, work_budget: int = 0, device_bytes: int = 0, stream=None,
-                     stop_rule: int = 0) -> int:
-    o = md_server_opts(slots, work_budget, device_bytes, stream, stop_rule)
+                     stop_rule: int = 0, heavy: int = 0) -> int:
+    o = md_server_opts(slots, work_budget, device_bytes, stream, stop_rule, heavy)
     s = ctypes.c_void_p()
     _check(lib.md_server_create(ctypes.byref(o), ctypes.byref(s)), "md_server_create")
     return s.value

@@ -9,6 +9,12 @@
 // the middle of another code's run share every following tick with it, so their work
 // overlaps on the device; results are identical to md_compute because every code's bounds,
 // level order and records are its own.
+//
+// Requests whose estimated work reaches the heavy threshold do not enter the slots: a second
+// worker thread runs them one at a time as single-code computations (md_compute, whose large
+// levels run on the tensor cores) on a stream of the server's own, so their levels neither
+// stretch the shared ticks nor wait behind them.  A slot code that runs past its planned
+// stages is handed to the same thread.
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -28,8 +34,10 @@ namespace {
 
 struct Request {
     uint64_t ticket = 0;
-    std::unique_ptr<PreparedCode> code;
+    std::unique_ptr<PreparedCode> code;   // slot requests only
     size_t bytes = 0;
+    std::vector<uint64_t> G;              // the caller's rows, for a single-code run
+    int n = 0, k = 0;
 };
 
 struct Done {
@@ -41,15 +49,23 @@ struct Done {
 }  // namespace
 
 constexpr int kTicksPerRound = 8;
+// Default heavy threshold: from about 10^9 estimated combinations a code fills the GPU on its
+// own for long enough that running it alone is quicker than sharing ticks; on a Poisson
+// stream of codes n = 64..200 it gave the lowest latencies of 10^8..3*10^9 (the spread was
+// a few percent).
+constexpr uint64_t kServeHeavyDefault = 1ull << 30;
 
 struct md_server {
     md_server_opts opts{};
     Engine eng;
     cudaStream_t own = nullptr;
-    std::thread worker;
+    cudaStream_t heavy_stream = nullptr;
+    std::thread worker, heavy_worker;
     std::mutex mu;
-    std::condition_variable cv;
+    std::condition_variable cv, heavy_cv;
     std::deque<Request> pending;
+    std::deque<Request> heavy_queue;          // single-code runs, in submission order
+    volatile int heavy_cancel = 0;            // set by md_server_destroy: ends a running one
     std::map<int, Request> resident;          // slot -> request
     std::map<uint64_t, Done> done;
     std::set<uint64_t> live;                  // submitted and not yet returned by a poll
@@ -60,7 +76,51 @@ struct md_server {
     PlanOptions po;
 
     void run();
+    void run_heavy();
+    void to_heavy(Request &&r);
 };
+
+// One request as a single-code computation on stream `st`.
+static Done single_code(const Request &r, cudaStream_t st, int stop_rule, volatile int *cancel) {
+    md_options oi;
+    md_options_init(&oi);
+    oi.stream = st;
+    oi.stop_rule = stop_rule;
+    oi.cancel_flag = cancel;
+    Done d;
+    d.witness.assign((size_t)(r.n + 63) / 64, 0);
+    md_handle h = nullptr;
+    int di = -1;
+    int rc = md_create_ex(r.G.data(), r.n, r.k, &oi, &h);
+    if (rc == MD_OK) rc = md_compute(h, &di, d.witness.data());
+    if (h) md_destroy(h);
+    d.status = rc;
+    d.d = rc == MD_OK ? di : -1;
+    return d;
+}
+
+void md_server::to_heavy(Request &&r) {
+    std::lock_guard<std::mutex> lk(mu);
+    heavy_queue.push_back(std::move(r));
+    heavy_cv.notify_one();
+}
+
+void md_server::run_heavy() {
+    for (;;) {
+        Request r;
+        {
+            std::unique_lock<std::mutex> lk(mu);
+            heavy_cv.wait(lk, [&] { return stop.load() || !heavy_queue.empty(); });
+            if (stop.load()) return;
+            r = std::move(heavy_queue.front());
+            heavy_queue.pop_front();
+        }
+        Done d = single_code(r, heavy_stream, opts.stop_rule, &heavy_cancel);
+        std::lock_guard<std::mutex> lk(mu);
+        if (d.status == MD_ECUDA) fatal = MD_ECUDA;
+        done[r.ticket] = std::move(d);
+    }
+}
 
 void md_server::run() {
     std::vector<BState> st;
@@ -119,26 +179,26 @@ void md_server::run() {
         }
         for (int s : finished) {
             // only this thread modifies `resident`, so reading it without the lock is safe
-            const Request &r = resident[s];
+            Request &r = resident[s];
             CodeResult res;
             int rc = eng.collect(s, *r.code, st[s], &res);
             eng.release(s);
-            if (rc == MD_OK && res.status == MD_EAGAIN_INTERNAL) {
-                // rare: the run went past the planned stages; finish it as a single code
-                const Code &cd = r.code->code;
-                md_options oi;
-                md_options_init(&oi);
-                oi.stream = eng.stream();
-                md_handle h = nullptr;
-                int di = -1;
-                res.witness.assign(cd.nw64, 0);
-                int r2 = md_create_ex(cd.G.data(), cd.n, cd.k, &oi, &h);
-                if (r2 == MD_OK) r2 = md_compute(h, &di, res.witness.data());
-                if (h) md_destroy(h);
-                res.status = r2;
-                res.d = r2 == MD_OK ? di : -1;
-            }
             free_slots.push_back(s);
+            if (rc == MD_OK && res.status == MD_EAGAIN_INTERNAL) {
+                // rare: the run went past the planned stages; it is finished as a single code
+                Request h;
+                h.ticket = r.ticket;
+                h.G = std::move(r.G);
+                h.n = r.n;
+                h.k = r.k;
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    bytes_in_use -= r.bytes;
+                    resident.erase(s);
+                }
+                to_heavy(std::move(h));
+                continue;
+            }
             Done d;
             d.status = rc != MD_OK ? rc : res.status;
             d.d = res.d;
@@ -167,6 +227,12 @@ int md_server_create(const md_server_opts *opts, md_server **out) {
         if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess) { delete s; return MD_ECUDA; }
         stream = s->own;
     }
+    s->opts.heavy = s->opts.heavy ? s->opts.heavy : kServeHeavyDefault;
+    if (cudaStreamCreateWithFlags(&s->heavy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (s->own) cudaStreamDestroy(s->own);
+        delete s;
+        return MD_ECUDA;
+    }
     // small work items keep the idle tail at the end of every tick short
     s->po.chunk_log2 = 16;
     s->po.stop_rule = s->opts.stop_rule;
@@ -175,10 +241,12 @@ int md_server_create(const md_server_opts *opts, md_server **out) {
     int rc = s->eng.init(s->opts.slots, stream, 1ull << 28, 0);
     if (rc != MD_OK) {
         if (s->own) cudaStreamDestroy(s->own);
+        cudaStreamDestroy(s->heavy_stream);
         delete s;
         return rc;
     }
     s->worker = std::thread([s] { s->run(); });
+    s->heavy_worker = std::thread([s] { s->run_heavy(); });
     *out = s;
     return MD_OK;
 }
@@ -190,15 +258,28 @@ int md_server_submit(md_server *s, const uint64_t *G, int n, int k, uint64_t *ti
     if (!r.code) return MD_ENOMEM;
     int rc = prepare_code(G, n, k, s->po, 0, s->opts.work_budget, r.code.get());
     if (rc != MD_OK) return rc;
-    r.bytes = r.code->header_bytes + r.code->h2_bytes;
-    if (r.bytes > s->opts.device_bytes) return MD_ENOMEM;
+    r.n = n;
+    r.k = k;
+    r.G.assign(G, G + (size_t)k * ((n + 63) / 64));
+    const bool heavy = s->opts.heavy != UINT64_MAX && r.code->est_work >= (double)s->opts.heavy;
+    if (heavy) {
+        r.code.reset();
+    } else {
+        r.bytes = r.code->header_bytes + r.code->h2_bytes;
+        if (r.bytes > s->opts.device_bytes) return MD_ENOMEM;
+    }
     std::lock_guard<std::mutex> lk(s->mu);
     if (s->fatal != MD_OK) return s->fatal;
     r.ticket = s->next_ticket++;
     *ticket = r.ticket;
     s->live.insert(r.ticket);
-    s->pending.push_back(std::move(r));
-    s->cv.notify_one();
+    if (heavy) {
+        s->heavy_queue.push_back(std::move(r));
+        s->heavy_cv.notify_one();
+    } else {
+        s->pending.push_back(std::move(r));
+        s->cv.notify_one();
+    }
     return MD_OK;
 }
 
@@ -217,11 +298,18 @@ int md_server_poll(md_server *s, uint64_t ticket, int *d, uint64_t *witness, int
 
 void md_server_destroy(md_server *s) {
     if (!s) return;
-    s->stop.store(true);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop.store(true);
+        s->heavy_cancel = 1;                  // a running single-code computation ends early
+    }
     s->cv.notify_all();
+    s->heavy_cv.notify_all();
     if (s->worker.joinable()) s->worker.join();
+    if (s->heavy_worker.joinable()) s->heavy_worker.join();
     s->eng.release_all();
     if (s->own) cudaStreamDestroy(s->own);
+    if (s->heavy_stream) cudaStreamDestroy(s->heavy_stream);
     delete s;
 }
 

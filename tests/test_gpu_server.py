@@ -131,3 +131,43 @@ def test_server_trace_sample(B):
             assert d == ds and np.array_equal(wit, ws)
     finally:
         B.md_server_destroy(s)
+
+
+def test_server_heavy_route_equals_oracle(B):
+    """With a low heavy threshold, the heavier requests of the trace run as single-code
+    computations on the server's second worker while the others share the slots; every result
+    equals the oracle and md_compute."""
+    s = B.md_server_create(slots=8, work_budget=3 * 10 ** 9, heavy=10 ** 7)
+    try:
+        tickets = []
+        for t, G, n, k in I.serving_trace(40):
+            try:
+                tickets.append((B.md_server_submit(s, G, n, k), G, n, k))
+            except B.MDError as e:
+                assert e.code == B.MD_EBUDGET
+        outs = [wait(B, s, tk, n) for tk, G, n, k in tickets]
+        for (tk, G, n, k), (d, wit, st) in zip(tickets, outs):
+            assert st == B.MD_OK
+            assert_oracle(G, n, k, d, wit)
+    finally:
+        B.md_server_destroy(s)
+    # every request in the slots (the threshold out of reach) gives the same answers
+    s = B.md_server_create(slots=8, work_budget=3 * 10 ** 9, heavy=2 ** 64 - 1)
+    try:
+        again = [wait(B, s, B.md_server_submit(s, G, n, k), n) for tk, G, n, k in tickets]
+        assert [(d, list(w)) for d, w, st in again] == [(d, list(w)) for d, w, st in outs]
+    finally:
+        B.md_server_destroy(s)
+
+
+def test_server_destroy_ends_running_heavy_request(B):
+    """md_server_destroy cancels a single-code computation in flight (rand200x100 runs for
+    about half a minute) instead of waiting for it to finish."""
+    s = B.md_server_create(slots=2)
+    G, n, k = I.single_code("rand200x100")
+    tk = B.md_server_submit(s, G, n, k)
+    time.sleep(1.0)
+    assert B.md_server_poll(s, tk, n) is None
+    t0 = time.time()
+    B.md_server_destroy(s)
+    assert time.time() - t0 < 5.0
