@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--verbose", action="store_true", help="per-level records on stderr")
     ap.add_argument("--batch-count", type=int, default=2048)
+    ap.add_argument("--batch-workers", type=int, default=0,
+                    help="threads running the batch's single-code computations (0 = library default 2)")
     ap.add_argument("--chunk-log2", type=int, default=0, help="log2 combinations per work item (0 = library default)")
     ap.add_argument("--batch-budget", type=float, default=1e10,
                     help="batch: per-code work budget in combinations (0 = every code)")
@@ -479,7 +481,7 @@ def batch_measure(args, B, inputs, budget, tune_cache=None):
     both.  budget = per-code estimated work limit (0 = every code)."""
     import torch
     codes = inputs.batch_codes(count=args.batch_count)
-    base = B.md_options_init(work_budget=budget)
+    base = B.md_options_init(work_budget=budget, batch_workers=args.batch_workers)
     t0 = time.perf_counter()
     opt = B.md_batch_tune(codes, base, tune_cache)
     t_tune = time.perf_counter() - t0
@@ -511,7 +513,8 @@ def batch_measure(args, B, inputs, budget, tune_cache=None):
             "tuned": {"chunk_log2": opt.chunk_log2, "blocks_per_sm": opt.blocks_per_sm,
                       "batch_heavy": opt.batch_heavy, "seconds": t_tune},
             "config": {"workload": "%d random codes, seed 4, n~U{48..160}, k~U{n/3..n/2}" % len(codes),
-                       "work_budget": budget, "histogram_done_skipped_by_n": hist}}
+                       "work_budget": budget, "batch_workers": opt.batch_workers or 2,
+                       "histogram_done_skipped_by_n": hist}}
 
 
 def serve_measure(args, B, inputs):

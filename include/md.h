@@ -126,13 +126,18 @@ typedef struct md_options {
     void (*dev_free)(void *ptr, void *alloc_ctx);
     void *alloc_ctx;
     uint64_t batch_heavy;     /* md_batch: codes whose estimated work (combinations until L >= U
-                                 for a random code of that shape) reaches this run one by one
-                                 as single-code computations, with the tensor-core levels, after
-                                 the shared schedule of the others (such a code fills the GPU by
-                                 itself); 0 = default 2^34, UINT64_MAX = none */
+                                 for a random code of that shape) reaches this run as
+                                 single-code computations, with the tensor-core levels (such a
+                                 code fills the GPU by itself; see batch_workers), while the
+                                 others share rounds; 0 = default 2^34, UINT64_MAX = none */
     int autotune;             /* md_batch: 1 = first pick chunk_log2, blocks_per_sm and batch_heavy
                                  with md_batch_tune (cached in tune_cache when set) */
     const char *tune_cache;   /* md_batch_tune's JSON cache file (NULL = no cache) */
+    int batch_workers;        /* md_batch: threads that run the single-code computations side by
+                                 side, each on a stream of its own, largest estimated work first,
+                                 beside the shared rounds (0 = default 2).  With dev_alloc set
+                                 they run one by one on the calling thread, the only thread the
+                                 allocator is called from. */
 } md_options;
 
 /* Result details of the last md_compute on a handle. */

@@ -34,7 +34,8 @@ class md_options(ctypes.Structure):
                 ("stop_rule", ctypes.c_int), ("perm_trials", ctypes.c_int), ("perm_seed", ctypes.c_uint64),
                 ("tensor", ctypes.c_int), ("tensor_head", ctypes.c_int), ("test_stall", ctypes.c_int),
                 ("dev_alloc", ctypes.c_void_p), ("dev_free", ctypes.c_void_p), ("alloc_ctx", ctypes.c_void_p),
-                ("batch_heavy", ctypes.c_uint64), ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p)]
+                ("batch_heavy", ctypes.c_uint64), ("autotune", ctypes.c_int), ("tune_cache", ctypes.c_char_p),
+                ("batch_workers", ctypes.c_int)]
 
 # Prototypes of the allocator hook (md_options.dev_alloc / dev_free).
 DEV_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

@@ -532,12 +532,13 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
     std::vector<size_t> woffs(count);
     std::vector<PreparedCode *> ok_codes;
     std::vector<int> ok_index, heavy_index;
+    std::vector<std::pair<double, int>> heavy_work;
     size_t wtot = 0;
     int rounds = 0;
     prepare_codes(codes, count, po, o.max_stage, o.work_budget, prep, status,
                   o.plan_horizon > 0 ? o.plan_horizon : 3);
     // codes whose estimated work reaches batch_heavy fill the GPU on their own: they run as
-    // single-code computations (with the tensor-core levels) after the shared schedule
+    // single-code computations (with the tensor-core levels) beside the shared schedule
     const double heavy = o.batch_heavy ? (double)o.batch_heavy : (double)kBatchHeavyDefault;
     for (int i = 0; i < count; i++) {
         woffs[i] = wtot;
@@ -545,7 +546,7 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
         d[i] = -1;
         if (status[i] != MD_OK) continue;
         if (prep[i].est_work >= heavy) {
-            heavy_index.push_back(i);
+            heavy_work.emplace_back(-prep[i].est_work, i);
             prep[i] = PreparedCode();          // its plans are not needed
             continue;
         }
@@ -553,6 +554,9 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
         ok_index.push_back(i);
         rounds = std::max(rounds, (int)prep[i].plans.size());
     }
+    // largest estimated work first, so that the workers finish together
+    std::sort(heavy_work.begin(), heavy_work.end());
+    for (const auto &hw : heavy_work) heavy_index.push_back(hw.second);
     const int nc = (int)ok_codes.size();
     if (nc == 0 && heavy_index.empty()) return MD_OK;
     // NVTX ranges (no-ops unless a profiler is attached): the batch, its shared rounds and
@@ -568,7 +572,40 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
         s = own;
     }
     int rc = MD_OK;
-    if (nc > 0) {
+    // Single-code runs on worker threads, each with a stream of its own, while this thread runs
+    // the shared rounds: one code's host set-up, table builds and small levels then overlap
+    // another's tensor-core levels.  With the caller's allocator they stay on this thread.
+    const int nworkers = heavy_index.empty() || o.dev_alloc ? 0 : (o.batch_workers > 0 ? o.batch_workers : 2);
+    std::atomic<size_t> next_heavy{0};
+    std::atomic<int> heavy_rc{MD_OK};
+    std::vector<std::thread> workers;
+    int dev = 0;
+    if (nworkers > 0 && cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); rc = MD_ECUDA; }
+    for (int w = 0; rc == MD_OK && w < nworkers; w++)
+        workers.emplace_back([&, dev] {
+            cudaStream_t ws = nullptr;
+            if (cudaSetDevice(dev) != cudaSuccess || cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                int ok = MD_OK;
+                heavy_rc.compare_exchange_strong(ok, MD_ECUDA);
+                return;
+            }
+            nvtxRangePushA("md_batch single-code runs");
+            for (;;) {
+                if (heavy_rc.load() != MD_OK) break;
+                const size_t h = next_heavy.fetch_add(1);
+                if (h >= heavy_index.size()) break;
+                const int i = heavy_index[h];
+                status[i] = single_code_run(codes[i], o, ws, &d[i], witness ? witness + woffs[i] : nullptr);
+                if (status[i] == MD_ECUDA || status[i] == MD_ENOMEM) {
+                    int ok = MD_OK;
+                    heavy_rc.compare_exchange_strong(ok, status[i]);
+                }
+            }
+            nvtxRangePop();
+            cudaStreamDestroy(ws);
+        });
+    if (nc > 0 && rc == MD_OK) {
         nvtxRangePushA("md_batch shared rounds");
         RangePop rounds_pop;
         Engine eng;
@@ -612,13 +649,24 @@ extern "C" int md_batch(const md_code *codes, int count, const md_options *opt, 
             }
         }
     }
-    if (!heavy_index.empty()) nvtxRangePushA("md_batch single-code runs");
-    for (size_t h = 0; rc == MD_OK && h < heavy_index.size(); h++) {
-        const int i = heavy_index[h];
-        status[i] = single_code_run(codes[i], o, s, &d[i], witness ? witness + woffs[i] : nullptr);
-        if (status[i] == MD_ECUDA || status[i] == MD_ENOMEM) rc = status[i];
+    if (rc != MD_OK) {
+        int ok = MD_OK;
+        heavy_rc.compare_exchange_strong(ok, rc);             // the workers take no further code
     }
-    if (!heavy_index.empty()) nvtxRangePop();
+    for (std::thread &t : workers) t.join();
+    if (rc == MD_OK) rc = heavy_rc.load();
+    size_t ran = std::min(next_heavy.load(), heavy_index.size());     // single-code runs started
+    if (nworkers == 0 && !heavy_index.empty()) {
+        nvtxRangePushA("md_batch single-code runs");
+        for (; rc == MD_OK && ran < heavy_index.size(); ran++) {
+            const int i = heavy_index[ran];
+            status[i] = single_code_run(codes[i], o, s, &d[i], witness ? witness + woffs[i] : nullptr);
+            if (status[i] == MD_ECUDA || status[i] == MD_ENOMEM) rc = status[i];
+        }
+        nvtxRangePop();
+    }
+    // after a failure, the codes no run reached carry the batch's status
+    for (; ran < heavy_index.size(); ran++) status[heavy_index[ran]] = rc;
     if (own) cudaStreamDestroy(own);
     if (rc == MD_OK && bounds_status() != MD_OK) rc = MD_EINTERNAL;      // the debug build's range checks
     return rc;

@@ -115,6 +115,13 @@ struct PlanOptions {
 // ---- tensor-core levels (md_tc.cu) ----
 size_t tc_tables_bytes(int k, int q, int W);  // head table of one matrix
 int tc_smem_bytes(int k, int W, int optin, int *with_bsub);
+
+// Raise a kernel's dynamic shared-memory limit to the most the current device allows, once per
+// kernel and device (thread-safe).  The limit is an attribute of the kernel for the whole
+// process: set per launch to that launch's size, two threads launching the same kernel with
+// different sizes (distinct handles, batch workers) could lower it under each other's launch.
+// The occupancy of a launch still follows the size it requests.  Returns a cudaError_t value.
+int allow_full_smem(const void *kernel);
 uint64_t tc_level_items(int k, int g, int q, int smin, int W);
 int tc_split_point(int k, int q);   // s_min of the two-phase split (see md_tc.cu)
 size_t tc_heads_bytes(uint64_t nheads, int W);

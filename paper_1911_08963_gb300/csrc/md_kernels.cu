@@ -26,6 +26,9 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <vector>
 
 #include "md_device.cuh"
@@ -172,26 +175,26 @@ template <int W, int WP>
 cudaError_t launch_kind(const LevelArgs &a, int kind, int blocks, int threads, size_t smem, cudaStream_t s) {
     if (kind == KIND_SIMPLE) {
         auto kern = simple_kernel<W, WP>;
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_full_smem((const void *)kern);
         kern<<<blocks, threads, smem, s>>>(a);
     } else if (kind == KIND_SPLIT2) {
         if (a.h2_in_smem) {
             auto kern = split_kernel<W, WP, 2, true>;
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            allow_full_smem((const void *)kern);
             kern<<<blocks, threads, smem, s>>>(a);
         } else {
             auto kern = split_kernel<W, WP, 2, false>;
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            allow_full_smem((const void *)kern);
             kern<<<blocks, threads, smem, s>>>(a);
         }
     } else {
         if (a.h2_in_smem) {
             auto kern = split_kernel<W, WP, 3, true>;
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            allow_full_smem((const void *)kern);
             kern<<<blocks, threads, smem, s>>>(a);
         } else {
             auto kern = split_kernel<W, WP, 3, false>;
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            allow_full_smem((const void *)kern);
             kern<<<blocks, threads, smem, s>>>(a);
         }
     }
@@ -243,12 +246,31 @@ int level_smem_bytes(int k, int WP, bool h2_in_smem) {
     return (int)(words * 4);
 }
 
+int allow_full_smem(const void *kernel) {
+    static std::mutex mu;
+    static std::set<std::pair<int, const void *>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count({dev, kernel})) return cudaSuccess;
+    cudaFuncAttributes fa{};
+    int optin = 0;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    if (e == cudaSuccess) done.insert({dev, kernel});
+    else cudaGetLastError();
+    return (int)e;
+}
+
 int level_blocks_per_sm(int kind, int W, bool h2s, int threads, size_t smem) {
     int nb = 0;
     cudaError_t e = cudaSuccess;
 #define MDL_OCC(KERN)                                                                          \
     do {                                                                                       \
-        cudaFuncSetAttribute(KERN, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);    \
+        allow_full_smem((const void *)KERN);                                                  \
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, KERN, threads, smem);           \
     } while (0)
 #define MDL_OCC_W(WW, WPP)                                                                     \

@@ -60,6 +60,7 @@ struct md_server {
     Engine eng;
     cudaStream_t own = nullptr;
     cudaStream_t heavy_stream = nullptr;
+    int device = 0;                           // the creating thread's device, made current in both workers
     std::thread worker, heavy_worker;
     std::mutex mu;
     std::condition_variable cv, heavy_cv;
@@ -106,6 +107,12 @@ void md_server::to_heavy(Request &&r) {
 }
 
 void md_server::run_heavy() {
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        std::lock_guard<std::mutex> lk(mu);
+        fatal = MD_ECUDA;
+        return;
+    }
     for (;;) {
         Request r;
         {
@@ -123,6 +130,12 @@ void md_server::run_heavy() {
 }
 
 void md_server::run() {
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        std::lock_guard<std::mutex> lk(mu);
+        fatal = MD_ECUDA;
+        return;
+    }
     std::vector<BState> st;
     std::vector<int> free_slots;
     for (int s = opts.slots - 1; s >= 0; s--) free_slots.push_back(s);
@@ -220,6 +233,7 @@ int md_server_create(const md_server_opts *opts, md_server **out) {
     md_server *s = new (std::nothrow) md_server();
     if (!s) return MD_ENOMEM;
     if (opts) s->opts = *opts;
+    if (cudaGetDevice(&s->device) != cudaSuccess) { cudaGetLastError(); delete s; return MD_ECUDA; }
     if (s->opts.slots <= 0) s->opts.slots = 64;
     if (s->opts.device_bytes == 0) s->opts.device_bytes = (size_t)256 << 20;
     cudaStream_t stream = (cudaStream_t)s->opts.stream;

@@ -1022,7 +1022,7 @@ __global__ void tc_heads_kernel(const uint32_t *rows, const unsigned long long *
 template <int W>
 cudaError_t launch_tc_w(const TcArgs &a, int blocks, size_t smem, cudaStream_t s) {
     auto kern = tc_kernel<W>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = (cudaError_t)allow_full_smem((const void *)kern);
     if (e != cudaSuccess) return e;
     kern<<<blocks, kTcThreads, smem, s>>>(a);
     return cudaGetLastError();

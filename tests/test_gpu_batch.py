@@ -109,16 +109,52 @@ def test_batch_per_matrix_bound(B):
 
 @pytest.mark.parametrize("heavy", [1 << 12, 1 << 20, (1 << 64) - 1])
 def test_batch_heavy_codes_run_alone(B, heavy):
-    """Codes whose estimated work reaches batch_heavy run one by one as single-code
-    computations (tensor-core levels forced on, so the small codes here reach that kernel too)
-    after the shared schedule of the others; every result equals the oracle's, whichever
-    route each code takes (2^12: most codes alone; 2^20: a mix; 2^64 - 1: none)."""
+    """Codes whose estimated work reaches batch_heavy run as single-code computations on two
+    worker threads (tensor-core levels forced on, so the small codes here reach that kernel
+    too) beside the shared schedule of the others; every result equals the oracle's,
+    whichever route each code takes (2^12: most codes alone; 2^20: a mix; 2^64 - 1: none)."""
     codes = mixed_codes()
     d, wits, st = B.md_batch(codes, B.md_options_init(batch_heavy=heavy, tensor=2, tensor_head=3))
     assert st == [B.MD_OK] * len(codes)
     for (G, n, k), di, wi in zip(codes, d, wits):
         res = O.bz(G, n, k, threads=8)
         assert di == res.d and np.array_equal(wi, res.witness), (n, k, heavy)
+
+
+def test_batch_workers_give_the_same_results(B):
+    """The single-code runs give the same statuses, d and witnesses on one, two or four worker
+    threads, and on the calling thread when a caller's allocator is set (the allocator is only
+    ever called from that thread)."""
+    import ctypes
+    import threading
+    torch = pytest.importorskip("torch")
+    codes = mixed_codes()
+
+    def same(a, b):
+        return a[0] == b[0] and a[2] == b[2] and all(np.array_equal(x, y) for x, y in zip(a[1], b[1]))
+
+    ref = B.md_batch(codes, B.md_options_init(batch_heavy=1 << 12, batch_workers=1))
+    assert ref[2] == [B.MD_OK] * len(codes)
+    for w in (2, 4):
+        assert same(B.md_batch(codes, B.md_options_init(batch_heavy=1 << 12, batch_workers=w)), ref), w
+    caller = threading.get_ident()
+    seen, live = set(), {}
+
+    def alloc(nbytes, ctx):
+        seen.add(threading.get_ident())
+        t = torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device="cuda")
+        live[t.data_ptr()] = t
+        return t.data_ptr()
+
+    def free(ptr, ctx):
+        live.pop(ptr, None)
+
+    fa, ff = B.DEV_ALLOC(alloc), B.DEV_FREE(free)
+    opt = B.md_options_init(batch_heavy=1 << 12, batch_workers=4)
+    opt.dev_alloc = ctypes.cast(fa, ctypes.c_void_p)
+    opt.dev_free = ctypes.cast(ff, ctypes.c_void_p)
+    assert same(B.md_batch(codes, opt), ref)
+    assert seen == {caller} and not live
 
 
 def test_batch_tune_picks_cached_valid_options(B, tmp_path):
