@@ -383,6 +383,19 @@ def run_ours(args):
         "d_after_stages": infos[0]["d"],
     }
 
+    if rank == 0 and roofline.get("bound") == "tensor":
+        # the tensor pipe's fp8 rate measured on this GPU (after the timed region), at the SM
+        # clock the timed region ran at: a second denominator beside the cuBLAS-derived peak
+        rate = B.md_mma_rate()
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clocks.get("sm_mhz") or measured_peaks().get("sm_max_mhz") or NOMINAL_MAX_MHZ
+        peak_cm = rate * sms * mhz * 1e6 / 1e12
+        roofline["clock_matched"] = {
+            "peak": peak_cm, "unit": "TFLOP/s", "flops_per_sm_per_clk": rate,
+            "basis": "md_mma_rate on this GPU: %.0f e4m3 flops/clk/SM x %d SMs x %.0f MHz (median SM clock "
+                     "of the timed region)" % (rate, sms, mhz),
+            "frac": roofline["achieved"] / peak_cm, "frac_method": roofline["method"]["achieved"] / peak_cm}
+
     if rank == 0 and not args.no_e2e:
         # end to end through the C ABI from host buffers: create (host G), compute, destroy
         opt_e = B.md_options_init(max_stage=args.max_stage, filter=args.filter, tensor=args.tensor)

@@ -265,6 +265,15 @@ void md_destroy(md_handle h);
    median over SMs).  The popcount kernels' roofline is this rate x SMs x the SM clock. */
 int md_popc_rate(double *per_sm_per_clk);
 
+/* Measurement utility (no counterpart in the paper): the dense fp8 (e4m3) throughput of the
+   current GPU's tensor pipe in flops per SM per clock.  In one block per SM, two threads issue
+   tcgen05.mma kind::f8f6f4 (M = 128, N = 256, K = 32, +-1 operands) back to back into two
+   accumulators, as the tensor-core level kernel's two issuers do; clock64 cycles, median over
+   SMs.  This rate x SMs x the SM clock is the fp8 peak at that clock, a denominator for the
+   tensor-core kernel's roofline beside the cuBLAS-derived one.  Returns MD_ETIMEOUT if a chain
+   did not complete within the kernel's time bound, MD_ECUDA on a failed CUDA call. */
+int md_mma_rate(double *flops_per_sm_per_clk);
+
 /* The range-checked build (compiled with -DMD_DEBUG_BOUNDS; paper_1911_08963_gb300.build
    builds it as libmd_debug.so): every index into the shared-memory rows and pair tables, the
    binomial tables, the work tables, and the tensor-core kernel's tables, tiles and head slices

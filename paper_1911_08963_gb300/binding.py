@@ -92,6 +92,7 @@ PROTOTYPES = {
                                              ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p, ip,
                                              u64p]),
     "md_popc_rate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
+    "md_mma_rate": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double)]),
     "md_debug_bounds": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
     "md_destroy": (None, [ctypes.c_void_p]),
     "md_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -247,6 +248,13 @@ def md_popc_rate() -> float:
     """POPC lane-operations per SM per clock on the current GPU (include/md.h)."""
     r = ctypes.c_double()
     _check(lib.md_popc_rate(ctypes.byref(r)), "md_popc_rate")
+    return r.value
+
+
+def md_mma_rate() -> float:
+    """Dense e4m3 tensor-pipe flops per SM per clock on the current GPU (include/md.h)."""
+    r = ctypes.c_double()
+    _check(lib.md_mma_rate(ctypes.byref(r)), "md_mma_rate")
     return r.value
 
 

@@ -62,6 +62,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "md_device.cuh"
 #include "md_internal.h"
@@ -1019,6 +1020,73 @@ __global__ void tc_heads_kernel(const uint32_t *rows, const unsigned long long *
     }
 }
 
+// Tensor-pipe probe: threads 0 and 32 (warps 0 and 1) each issue `iters` e4m3 MMAs (M = 128,
+// N = 256, K = 32) back to back into an accumulator of their own, as the level kernel's two
+// issuers do; operands are +-1 tiles in shared memory in the level kernel's layout.  cyc[b] =
+// block b's clock64 cycles from the first issue to the completion of both chains; err = 1 if a
+// chain did not complete within the time bound (the block then still waits for it, bounded,
+// before freeing its tensor memory).  The dynamic shared memory asked for keeps one block per SM.
+constexpr int kProbeThreads = 64;
+__global__ void __launch_bounds__(kProbeThreads) mma_probe_kernel(unsigned iters, unsigned long long *cyc, int *err) {
+    extern __shared__ __align__(1024) unsigned char probe_raw[];
+    unsigned char *tiles = reinterpret_cast<unsigned char *>(((uintptr_t)probe_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) unsigned long long done[2];
+    __shared__ uint32_t taddr;
+    __shared__ unsigned long long t0s[2], t1s[2];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kBytes = (kTcM + kTcN) * 32;           // one tail tile and one head slice, W = 1
+    for (int i = threadIdx.x; i < kBytes / 4; i += blockDim.x) {
+        uint32_t h = (uint32_t)i * 0x9E3779B9u;
+        h ^= h >> 15;
+        uint32_t v = 0;
+        for (int b = 0; b < 4; b++) v |= (((h >> b) & 1u) ? 0xB8u : 0x38u) << (8 * b);
+        reinterpret_cast<uint32_t *>(tiles)[i] = v;
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(saddr(&done[0]), 1);
+        mbar_init(saddr(&done[1]), 1);
+        fence_mbar_init();
+    }
+    fence_async_smem();                                  // the tiles, for the tensor core's reads
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&taddr)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before();
+    __syncthreads();
+    tc_after();
+    const uint32_t tmem = taddr;
+    if (lane == 0) {
+        const int me = warp;
+        const uint64_t adesc = smem_desc(saddr(tiles), 128u, 256u);
+        const uint64_t bdesc = smem_desc(saddr(tiles + kTcM * 32), 128u, 256u);
+        const uint32_t idesc = idesc_e4m3(kTcN);
+        const uint32_t d = tmem + (uint32_t)(me * kTcN);
+        const unsigned long long t0 = clock64();
+        for (unsigned i = 0; i < iters; i++) mma_e4m3(d, adesc, bdesc, idesc, i > 0 ? 1u : 0u);
+        mma_commit(saddr(&done[me]));
+        const uint64_t g0 = gtimer();
+        bool ok = true;
+        while (!mbar_test(saddr(&done[me]), 0))
+            if (gtimer() - g0 > kWaitNs) { ok = false; break; }
+        t0s[me] = t0;
+        t1s[me] = clock64();
+        if (!ok) {
+            atomicExch(err, 1);
+            mbar_drain(saddr(&done[me]), 0);
+        }
+    }
+    tc_before();
+    __syncthreads();
+    if (threadIdx.x == 0) cyc[blockIdx.x] = max(t1s[0], t1s[1]) - min(t0s[0], t0s[1]);
+    if (warp == 0) {
+        tc_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
 template <int W>
 cudaError_t launch_tc_w(const TcArgs &a, int blocks, size_t smem, cudaStream_t s) {
     auto kern = tc_kernel<W>;
@@ -1135,3 +1203,44 @@ int launch_tc_level(const unsigned char *tables, const unsigned char *tables2, i
 }
 
 }  // namespace mdl
+
+// Dense e4m3 flops per SM per clock of the tensor pipe, measured (median over one block per SM).
+extern "C" int md_mma_rate(double *flops_per_sm_per_clk) {
+    using namespace mdl;
+    if (!flops_per_sm_per_clk) return MD_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms < 1) {
+        cudaGetLastError();
+        return MD_ECUDA;
+    }
+    const int smem = 150 * 1024;                        // more than half an SM's shared memory
+    unsigned long long *cyc = nullptr;
+    int *err = nullptr;
+    if (cudaFuncSetAttribute(mma_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+        cudaMalloc(&cyc, sizeof(unsigned long long) * sms) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (cyc) cudaFree(cyc);
+        return MD_ECUDA;
+    }
+    const unsigned iters = 1u << 13;
+    int herr = 0;
+    bool ok = cudaMemset(err, 0, sizeof(int)) == cudaSuccess;
+    if (ok) {
+        mma_probe_kernel<<<sms, kProbeThreads, smem>>>(256u, cyc, err);          // warm-up
+        mma_probe_kernel<<<sms, kProbeThreads, smem>>>(iters, cyc, err);
+    }
+    std::vector<unsigned long long> h(sms);
+    ok = ok && cudaGetLastError() == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+         cudaMemcpy(h.data(), cyc, sizeof(unsigned long long) * sms, cudaMemcpyDeviceToHost) == cudaSuccess &&
+         cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess;
+    cudaFree(cyc);
+    cudaFree(err);
+    if (!ok) { cudaGetLastError(); return MD_ECUDA; }
+    if (herr) return MD_ETIMEOUT;
+    std::sort(h.begin(), h.end());
+    const double med = (double)h[h.size() / 2];
+    if (med <= 0) return MD_EINTERNAL;
+    *flops_per_sm_per_clk = 2.0 * iters * (2.0 * kTcM * kTcN * 32) / med;
+    return MD_OK;
+}
