@@ -54,6 +54,16 @@ DATA = ("synthetic: random code G=[I_100|R], R i.i.d. Bernoulli(1/2) from SplitM
         "(the first draw; R is invertible)")
 
 
+def data_string(workload: str) -> str:
+    """The `data` field of both arms for a single-code workload."""
+    if workload == "rand200x100":
+        return DATA
+    from paper_1911_08963_gb300 import inputs
+    c = inputs.SINGLE[workload]
+    return ("synthetic: random code G=[I_%d|R], R i.i.d. Bernoulli(1/2) from SplitMix64 seed %d "
+            "(draw %d: the first invertible R)" % (c["k"], c["seed"], c["skip"] + 1))
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -73,6 +83,9 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batch lines (all 2048 codes, and under 1e10)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving line")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--oracle-full", action="store_true",
+                    help="reference arm, workloads with k <= 64: also time the complete oracle run to d "
+                         "(and the 2^k brute force for k <= 32) on all host cores")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--verbose", action="store_true", help="per-level records on stderr")
     ap.add_argument("--batch-count", type=int, default=2048)
@@ -167,8 +180,10 @@ def dist_env():
 
 def workload_config(args, n, k):
     """The `config` object shared by both arms."""
-    return {"workload": "random [%d,%d] seed 3, Brouwer-Zimmermann stages g=1..%d, every level complete"
-                        % (n, k, args.max_stage),
+    from paper_1911_08963_gb300 import inputs
+    seed = inputs.SINGLE[args.workload]["seed"] if args.workload in inputs.SINGLE else 3
+    return {"workload": "random [%d,%d] seed %d, Brouwer-Zimmermann stages g=1..%d, every level complete "
+                        "(or the run to d if it stops first)" % (n, k, seed, args.max_stage),
             "n": n, "k": k, "max_stage": args.max_stage, "filter": args.filter,
             "l2": "flushed between steps (512 MiB write); inputs are ~100 KB"}
 
@@ -278,7 +293,7 @@ def run_reference(args):
     G, n, k = inputs.single_code(args.workload)
     threads = os.cpu_count() or 1
     g = args.max_stage
-    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    per_step = 2.0 if args.oracle_full else max(2.0, 120.0 / max(1, args.steps + args.warmup))
     rates = []
     for i in range(args.warmup + args.steps):
         rate, size, dt = oracle_sample_rate(G, n, k, g, per_step, threads)
@@ -291,13 +306,24 @@ def run_reference(args):
         "impl": "reference", "metric": "codewords/s", "value": value, "unit": "codewords/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / len(rates),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
-        "data": DATA,
+        "data": data_string(args.workload),
         "config": workload_config(args, n, k),
         "cpu_baseline": {"value": value, "unit": "codewords/s", "cores": threads, "kind": "oracle",
                          "sample": "colex-rank prefix of level (g=%d, Gamma_1), %d combinations per step"
                                    % (g, rates[0][0])},
         "e2e": {"value": value, "unit": "codewords/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
+    if args.oracle_full and k <= 64:
+        # the whole computation on the host cores: Alg. 1 to d, and for k <= 32 the definition
+        t0 = time.perf_counter()
+        res = oracle.bz(G, n, k, threads=threads)
+        full = {"d": res.d, "seconds": time.perf_counter() - t0, "codewords": res.codewords,
+                "stop_stage": res.stop[0], "threads": threads}
+        if k <= 32:
+            t0 = time.perf_counter()
+            dbf, _ = oracle.bruteforce(G, n, k, threads=threads)
+            full["bruteforce"] = {"d": dbf, "seconds": time.perf_counter() - t0, "messages": (1 << k) - 1}
+        line["oracle_full"] = full
     print(json.dumps(line), flush=True)
     return 0
 
@@ -376,7 +402,7 @@ def run_ours(args):
         "metric": "codewords/s", "value": value, "unit": "codewords/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
-        "data": DATA,
+        "data": data_string(args.workload),
         "config": dict(workload_config(args, n, k), codewords_per_step=infos[0]["codewords"],
                        parallelism="replicas" if ws > 1 else "single GPU"),
         "roofline": roofline, "clocks": clocks, "gpu_launches": launches,
@@ -421,7 +447,7 @@ def run_ours(args):
                                 "sample": "colex-rank prefix of level (g=%d, Gamma_1): %d combinations, %.1f s"
                                           % (args.max_stage, size, dt)}
 
-    if rank == 0 and ws == 1 and not args.no_time_to_d and args.workload == "rand200x100":
+    if rank == 0 and ws == 1 and not args.no_time_to_d:
         opt_f = B.md_options_init(filter=args.filter, tensor=args.tensor, stream=stream.cuda_stream)
         hf = B.md_create(G, n, k, opt_f)
         e0 = torch.cuda.Event(enable_timing=True)
