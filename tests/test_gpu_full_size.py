@@ -118,3 +118,31 @@ def test_full_rand200x100_popcount_kernels_agree(B, default_run):
     assert (info0["key_g"], info0["key_j"], info0["key_rank"]) == (info["key_g"], info["key_j"], info["key_rank"])
     assert levels0 == levels
     assert info0["complete"] == 1 and info0["lower_bound"] == info["lower_bound"]
+
+
+def test_full_rand200x100_stage11_windows_hold_nothing_lighter(B, default_run):
+    """Stage 11 is where d is first reached and proven (L = 2 * 12 = 24).  The oracle scans
+    spread colex windows of 2^22 ranks in both of its levels (the first ranks, the last, and
+    six at seeded random offsets): no window holds a codeword lighter than d, and a window
+    holding a codeword of weight d belongs to a level whose record has weight d and a rank no
+    later than the window's first rank of that weight (the record is the level's first rank of its least
+    weight, and d is at most the U held before either level)."""
+    import math
+    G, n, k = I.single_code("rand200x100")
+    d, _, info, levels, gam = default_run
+    gams, _, _ = O.gammas(G, n, k)
+    rng = np.random.default_rng(11)
+    win = 1 << 22
+    total = math.comb(k, 11)
+    recs = {(g, j): (w, first) for g, j, w, first, _ in levels}
+    assert (11, 0) in recs and (11, 1) in recs
+    for j in (0, 1):
+        assert np.array_equal(gams[j], gam[j])
+        w_rec, first_rec = recs[(11, j)]
+        starts = [0, total - win] + [int(x) for x in rng.integers(0, total - win, size=6)]
+        for r0 in starts:
+            w, first = O.scan(gams[j], n, k, 11, r0, r0 + win, threads=THREADS)
+            assert w >= d, (j, r0, w)
+            if w == d:
+                # weight d is at most the U held before either level, so the level records it
+                assert w_rec == d and first >= first_rec, (j, r0, first, w_rec, first_rec)
