@@ -389,7 +389,9 @@ int md_server_create(const md_server_opts *opts, md_server **out);
 int md_server_submit(md_server *s, const uint64_t *G, int n, int k, uint64_t *ticket);
 /* MD_OK with *d, witness (ceil(n/64) words, may be NULL) and *status filled when done;
    MD_EBUSY while pending; MD_EINVAL for an unknown ticket.  A finished ticket is
-   released by the poll that returns it. */
+   released by the poll that returns it.  After a failed CUDA call the server takes no more
+   work: a request still waiting then completes with *status = that error (MD_ECUDA) and
+   *d = -1, so no caller polls MD_EBUSY forever. */
 int md_server_poll(md_server *s, uint64_t ticket, int *d, uint64_t *witness, int *status);
 void md_server_destroy(md_server *s);
 

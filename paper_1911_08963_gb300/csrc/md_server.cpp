@@ -117,14 +117,17 @@ void md_server::run_heavy() {
         Request r;
         {
             std::unique_lock<std::mutex> lk(mu);
-            heavy_cv.wait(lk, [&] { return stop.load() || !heavy_queue.empty(); });
-            if (stop.load()) return;
+            heavy_cv.wait(lk, [&] { return stop.load() || fatal != MD_OK || !heavy_queue.empty(); });
+            if (stop.load() || fatal != MD_OK) return;     // after a failed CUDA call: no more work
             r = std::move(heavy_queue.front());
             heavy_queue.pop_front();
         }
         Done d = single_code(r, heavy_stream, opts.stop_rule, &heavy_cancel);
         std::lock_guard<std::mutex> lk(mu);
-        if (d.status == MD_ECUDA) fatal = MD_ECUDA;
+        if (d.status == MD_ECUDA) {
+            fatal = MD_ECUDA;
+            cv.notify_all();
+        }
         done[r.ticket] = std::move(d);
     }
 }
@@ -143,6 +146,12 @@ void md_server::run() {
         std::vector<Request> admit;
         {
             std::unique_lock<std::mutex> lk(mu);
+            if (fatal != MD_OK) {
+                // a CUDA call failed (in either worker): finish what is resident with that error
+                for (auto &kv : resident) { Done d; d.status = fatal; done[kv.second.ticket] = std::move(d); }
+                resident.clear();
+                return;
+            }
             if (resident.empty() && pending.empty()) {
                 cv.wait_for(lk, std::chrono::milliseconds(2));
                 continue;
@@ -168,7 +177,10 @@ void md_server::run() {
                 done[r.ticket] = std::move(d);
                 bytes_in_use -= r.bytes;
                 free_slots.push_back(slot);
-                if (rc == MD_ECUDA) fatal = rc;
+                if (rc == MD_ECUDA) {
+                    fatal = rc;
+                    heavy_cv.notify_all();
+                }
                 continue;
             }
             std::lock_guard<std::mutex> lk(mu);
@@ -180,6 +192,7 @@ void md_server::run() {
         if (eng.tick(kTicksPerRound, true) != MD_OK || eng.read_states(st) != MD_OK) {
             std::lock_guard<std::mutex> lk(mu);
             fatal = MD_ECUDA;
+            heavy_cv.notify_all();
             for (auto &kv : resident) { Done d; d.status = MD_ECUDA; done[kv.second.ticket] = std::move(d); }
             resident.clear();
             return;
@@ -301,7 +314,15 @@ int md_server_poll(md_server *s, uint64_t ticket, int *d, uint64_t *witness, int
     if (!s || !d || !status) return MD_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
     auto it = s->done.find(ticket);
-    if (it == s->done.end()) return s->live.count(ticket) ? MD_EBUSY : MD_EINVAL;
+    if (it == s->done.end()) {
+        if (!s->live.count(ticket)) return MD_EINVAL;
+        if (s->fatal == MD_OK) return MD_EBUSY;
+        // the workers stopped taking work after a failed CUDA call: report it for this ticket
+        *d = -1;
+        *status = s->fatal;
+        s->live.erase(ticket);
+        return MD_OK;
+    }
     *d = it->second.d;
     *status = it->second.status;
     if (witness) std::memcpy(witness, it->second.witness.data(), it->second.witness.size() * 8);

@@ -158,14 +158,17 @@ def test_tensor_matches_split_kernel_stage10(B):
 def test_tensor_wide_rows_production_levels(B, n, k, gmax, seed):
     """Wide packed rows at production level sizes (the default rule picks the tensor cores for
     C(k, g) >= 2^28): W = 5..7, so tile sets of T = 2 and T = 1 tiles, up to five matrices
-    with a rank-deficient last one.  The records equal those of the popcount kernels and each
-    record's codeword (rows of Gamma_j at the record's colex rank) has the recorded weight."""
+    with a rank-deficient last one.  The records equal those of the popcount kernels, each
+    record's codeword (rows of Gamma_j at the record's colex rank) has the recorded weight,
+    and the oracle's scan of the 2^22 colex ranks ending at each record returns exactly the
+    record (no lighter codeword there, and none of its weight ranked earlier)."""
     import math
     G = T.pack(T.random_rows(n, k, seed), n)
     _, _, _, lev_tc = run_gpu(B, G, n, k, max_stage=gmax, tensor=1)
     _, _, _, lev_pc = run_gpu(B, G, n, k, max_stage=gmax, tensor=0)
     assert lev_tc == lev_pc
     assert any(math.comb(k, lv[0]) >= 1 << 28 for lv in lev_tc)
+    gams, _, _ = O.gammas(G, n, k)
     h = B.md_create(G, n, k, B.md_options_init())
     try:
         gam = {}
@@ -174,10 +177,13 @@ def test_tensor_wide_rows_production_levels(B, n, k, gmax, seed):
                 continue
             if j not in gam:
                 gam[j] = B.md_gamma(h, j, n, k)[0]
+                assert np.array_equal(gams[j], gam[j]), j
             row = np.zeros(gam[j].shape[1], dtype=np.uint64)
             for c in O.colex_unrank(first, g, k):
                 row ^= gam[j][c]
             assert sum(bin(int(x)).count("1") for x in row) == w, (g, j)
+            r0 = max(0, first + 1 - (1 << 22))
+            assert O.scan(gams[j], n, k, g, r0, first + 1, threads=THREADS) == (w, first), (g, j)
     finally:
         B.md_destroy(h)
 
