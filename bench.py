@@ -240,6 +240,16 @@ def roofline_line(args, n, k, top_g, nlaunch, per_launch_cw, per_launch_s, words
                          per_launch_s, "16 popc/clk/SM (an earlier probe) x 152 SMs x 2070 MHz max clock")
 
 
+def clock_matched(roofline, rate, sms, mhz):
+    """The tensor roofline's work against the tensor pipe's own e4m3 rate on this GPU:
+    md_mma_rate's flops per SM per clock x SMs x the SM clock (MHz) of the timed region."""
+    peak = rate * sms * mhz * 1e6 / 1e12
+    return {"peak": peak, "unit": "TFLOP/s", "flops_per_sm_per_clk": rate,
+            "basis": "md_mma_rate on this GPU: %.0f e4m3 flops/clk/SM x %d SMs x %.0f MHz (median SM clock "
+                     "of the timed region)" % (rate, sms, mhz),
+            "frac": roofline["achieved"] / peak, "frac_method": roofline["method"]["achieved"] / peak}
+
+
 def popc_roofline(per_sm_clk, sms, mhz, top_g, nlaunch, per_launch_cw, per_launch_s, basis):
     """Roofline of the popcount kernels (the split kernel of the deepest stage): one POPC per
     codeword (the popcount of the OR of the fewest packed words that bounds the weight; exact
@@ -412,15 +422,9 @@ def run_ours(args):
     if rank == 0 and roofline.get("bound") == "tensor":
         # the tensor pipe's fp8 rate measured on this GPU (after the timed region), at the SM
         # clock the timed region ran at: a second denominator beside the cuBLAS-derived peak
-        rate = B.md_mma_rate()
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = clocks.get("sm_mhz") or measured_peaks().get("sm_max_mhz") or NOMINAL_MAX_MHZ
-        peak_cm = rate * sms * mhz * 1e6 / 1e12
-        roofline["clock_matched"] = {
-            "peak": peak_cm, "unit": "TFLOP/s", "flops_per_sm_per_clk": rate,
-            "basis": "md_mma_rate on this GPU: %.0f e4m3 flops/clk/SM x %d SMs x %.0f MHz (median SM clock "
-                     "of the timed region)" % (rate, sms, mhz),
-            "frac": roofline["achieved"] / peak_cm, "frac_method": roofline["method"]["achieved"] / peak_cm}
+        roofline["clock_matched"] = clock_matched(roofline, B.md_mma_rate(), sms, mhz)
 
     if rank == 0 and not args.no_e2e:
         # end to end through the C ABI from host buffers: create (host G), compute, destroy

@@ -1,5 +1,6 @@
-"""bench.py's replica reduction across ranks (slowest time, summed codewords), with two gloo
-ranks on the CPU."""
+"""bench.py's host-side arithmetic: the replica reduction across ranks (slowest time, summed
+codewords, with two gloo ranks on the CPU), the roofline lines and the workload strings the
+two arms share."""
 import os
 import socket
 
@@ -72,3 +73,34 @@ def test_roofline_line_arithmetic():
     assert r["bound"] == "alu"
     assert r["peak"] == pytest.approx(16 * 152 * 2070e6 / 1e9)
     assert r["achieved"] == pytest.approx(1.7e13 / 5.0 / 1e9)
+
+
+def test_clock_matched_denominator():
+    """The clock-matched tensor roofline: md_mma_rate's flops per SM per clock x SMs x MHz;
+    16384 flops/clk/SM (one M = 128, N = 256, K = 32 MMA per 128 cycles) x 152 x 2070 MHz is
+    5155 TFLOP/s, and both fractions divide the line's own achieved figures by it."""
+    import types
+    import bench
+    r = bench.roofline_line(types.SimpleNamespace(tensor=1), 200, 100, 10, 4, 1.7e13, 1.5, 3)
+    c = bench.clock_matched(r, 16384.0, 152, 2070.0)
+    assert c["peak"] == pytest.approx(16384 * 152 * 2070e6 / 1e12)
+    assert c["peak"] == pytest.approx(5155.0, rel=1e-3)
+    assert c["frac"] == pytest.approx(r["achieved"] / c["peak"])
+    assert c["frac_method"] == pytest.approx(r["method"]["achieved"] / c["peak"])
+
+
+@pytest.mark.parametrize("workload", ["rand64x32", "rand128x64", "rand200x100"])
+def test_workload_strings_name_the_drawn_code(workload):
+    """Both arms print the same `data` and `config` for a workload, and they name that code's
+    own size and seed (the reference arm and ours call the same two functions)."""
+    import types
+    import bench
+    from paper_1911_08963_gb300 import inputs
+    c = inputs.SINGLE[workload]
+    args = types.SimpleNamespace(workload=workload, max_stage=10, filter=1)
+    cfg = bench.workload_config(args, c["n"], c["k"])
+    assert cfg["workload"].startswith("random [%d,%d] seed %d," % (c["n"], c["k"], c["seed"]))
+    data = bench.data_string(workload)
+    assert "I_%d|R" % c["k"] in data and "seed %d" % c["seed"] in data
+    if workload == "rand200x100":
+        assert data == bench.DATA
