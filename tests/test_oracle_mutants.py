@@ -34,6 +34,16 @@ MUTANTS = {
     "per_matrix_bound_too_strong": ("L += set_bound(i <= j ? g : g - 1, k, ranks[i]);", "L += set_bound(g, k, ranks[i]);"),
     "partial_set_rank_off": ("            ranks[m++] = r;\n", "            ranks[m++] = r - (r > 1);\n"),
     "weight_ignores_column0": ("for (int i = 0; i < nw; i++) w += __builtin_popcountll(row[i]);", "for (int i = 0; i < nw; i++) w += __builtin_popcountll(row[i] & (i ? ~0ull : ~1ull));"),
+    # the threaded parts: ranges split across threads and the results combined
+    "scan_threads_keep_later_tie": ("if (jobs[t].minw < bw) { bw = jobs[t].minw; br = jobs[t].first; }",
+                                    "if (jobs[t].minw <= bw) { bw = jobs[t].minw; br = jobs[t].first; }"),
+    "scan_ranges_shifted": ("jobs[t].r0 = r0 + span / nthreads * t + ((uint64_t)t < span % nthreads ? (uint64_t)t : span % nthreads);",
+                            "jobs[t].r0 = r0 + span / nthreads * t + ((uint64_t)t < span % nthreads ? (uint64_t)t : span % nthreads) - (t > 0);"),
+    "bruteforce_thread_start_not_gray": ("uint64_t x = J->lo ^ (J->lo >> 1);", "uint64_t x = J->lo;"),
+    "bruteforce_ranges_shifted": ("jobs[t].lo = total / nthreads * t + (t < (int)(total % nthreads) ? t : total % nthreads);",
+                                  "jobs[t].lo = total / nthreads * t + (t < (int)(total % nthreads) ? t : total % nthreads) - (t > 0);"),
+    "bruteforce_ranges_overlap": ("jobs[t].hi = jobs[t].lo + total / nthreads + (t < (int)(total % nthreads) ? 1 : 0);",
+                                  "jobs[t].hi = jobs[t].lo + total / nthreads + (t < (int)(total % nthreads) ? 1 : 0) + (t + 1 < nthreads);"),
 }
 
 

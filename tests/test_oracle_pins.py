@@ -106,12 +106,17 @@ def test_bruteforce_textbook(name):
 
 
 def test_bruteforce_threads_and_rank_deficiency():
+    """The message range split over 1, 2, 3, 5, 7 and 16 threads gives the whole weight
+    distribution of a random [70,14] code, each time equal to a Python enumeration of all
+    2^14 codewords (a range that overlaps, skips or shifts by one message shows up in it)."""
     rows = T.random_rows(70, 14, seed=3)
     G = T.pack(rows, 70)
-    d1, dist1 = O.bruteforce(G, 70, 14, threads=1)
-    d4, dist4 = O.bruteforce(G, 70, 14, threads=5)
-    assert d1 == d4 and np.array_equal(dist1, dist4)
-    assert d1 == min(T.wt(v) for v in T.all_codewords(rows)[1:])
+    want = T.weight_distribution(rows, 70)
+    assert sum(want) == 1 << 14
+    for threads in (1, 2, 3, 5, 7, 16):
+        d, dist = O.bruteforce(G, 70, 14, threads=threads)
+        assert [int(x) for x in dist] == want, threads
+        assert d == min(w for w in range(1, 71) if want[w])
     dup = T.pack(rows[:-1] + [rows[0]], 70)          # repeated row: rank 13
     d0, _ = O.bruteforce(dup, 70, 14)
     assert d0 == 0
@@ -349,3 +354,38 @@ def test_scan_ranges_compose():
     best = min(parts)          # (w, rank) lexicographic; ranges are disjoint
     assert best == whole
     assert O.scan(gams[0], 60, 24, g, 5, 5) == (61, (1 << 64) - 1)
+
+
+def test_scan_subranges_and_threads_against_enumeration():
+    """The scan of any colex-rank range [r0, r1), split over 1, 2, 3, 5 or 7 threads, returns
+    the least weight in that range and its first rank, as a Python enumeration of the same
+    g-subsets in colex order (tuples sorted by their reversed elements) finds them.  Small
+    ranges, ranges ending right after a level minimum, and whole levels are included, so a
+    split that drops, repeats or shifts a rank, or a tie resolved to a later thread, fails."""
+    n, k = 40, 14
+    rows = T.random_rows(n, k, 77)
+    G = T.pack(rows, n)
+    gams, _, _ = O.gammas(G, n, k)
+    grow = T.unpack(gams[0])
+    rng = np.random.default_rng(5)
+    for g in (1, 2, 3, 5):
+        combos = sorted(itertools.combinations(range(k), g), key=lambda c: c[::-1])
+        weights = []
+        for c in combos:
+            v = 0
+            for i in c:
+                v ^= grow[i]
+            weights.append(T.wt(v))
+        total = len(combos)
+        wmin = min(weights)
+        last_min = max(r for r, w in enumerate(weights) if w == wmin)
+        ranges = [(0, total), (0, last_min + 1), (last_min, total), (last_min, last_min + 1)]
+        for _ in range(12):
+            a, b = sorted(int(x) for x in rng.integers(0, total + 1, size=2))
+            if a < b:
+                ranges.append((a, b))
+        for r0, r1 in ranges:
+            w = min(weights[r0:r1])
+            want = (w, r0 + weights[r0:r1].index(w))
+            for threads in (1, 2, 3, 5, 7):
+                assert O.scan(gams[0], n, k, g, r0, r1, threads=threads) == want, (g, r0, r1, threads)
