@@ -39,6 +39,28 @@ MUTANTS = {
                                     "if (jobs[t].minw <= bw) { bw = jobs[t].minw; br = jobs[t].first; }"),
     "scan_ranges_shifted": ("jobs[t].r0 = r0 + span / nthreads * t + ((uint64_t)t < span % nthreads ? (uint64_t)t : span % nthreads);",
                             "jobs[t].r0 = r0 + span / nthreads * t + ((uint64_t)t < span % nthreads ? (uint64_t)t : span % nthreads) - (t > 0);"),
+    # the stage loop's bookkeeping and outputs
+    "codewords_count": ("evaluated += count;", "evaluated += count - (j > 0);"),
+    "stage_bound_lags": ("        for (int j = 0; j < m; j++) L += set_bound(g, k, ranks[j]);",
+                         "        for (int j = 0; j < m; j++) L += set_bound(g - 1, k, ranks[j]);"),
+    "witness_from_matrix0": ("xor_row(witness, Gam + ((size_t)key_j * k + c[i]) * nw, nw);",
+                             "xor_row(witness, Gam + ((size_t)0 * k + c[i]) * nw, nw);"),
+    "stop_after_g_late": ("if (stop_after_g > 0 && g >= stop_after_g) break;", "if (stop_after_g > 0 && g > stop_after_g) break;"),
+    "key_ties_later": ("if (w < U) { U = w; key_g = g; key_j = j; key_rank = first; }",
+                       "if (w <= U) { U = w; key_g = g; key_j = j; key_rank = first; }"),
+    "per_matrix_bound_off_by_one_matrix": ("L += set_bound(i <= j ? g : g - 1, k, ranks[i]);",
+                                           "L += set_bound(i < j ? g : g - 1, k, ranks[i]);"),
+    "level_count_field": ("rec[4] = (int64_t)count;", "rec[4] = (int64_t)count - (g > 1);"),
+    "scan_empty_weight": ("J->minw = J->n + 1;", "J->minw = J->n;"),
+    "colex_next_limit": ("int limit = (i + 1 < g) ? c[i + 1] : k;", "int limit = (i + 1 < g) ? c[i + 1] : k - 1;"),
+    "bruteforce_rank_check": ("if (dist[0] > 1) return 0;", "if (dist[0] > 2) return 0;"),
+    # the information sets (Section 2.1 as read here: leftover columns form the last set)
+    "rank1_last_set_dropped": ("        if (r > 0) {\n            for (int q = 0; q < nrem; q++)",
+                               "        if (r > 1) {\n            for (int q = 0; q < nrem; q++)"),
+    "full_set_order_rest_descending": ("            for (int col = 0; col < n; col++) if (!in_set[col]) order[pos++] = col;\n            ranks[m++] = k;",
+                                       "            for (int col = n - 1; col >= 0; col--) if (!in_set[col]) order[pos++] = col;\n            ranks[m++] = k;"),
+    "partial_set_order_rest_descending": ("            for (int col = 0; col < n; col++) if (!in_set[col]) order[pos++] = col;\n            ranks[m++] = r;",
+                                          "            for (int col = n - 1; col >= 0; col--) if (!in_set[col]) order[pos++] = col;\n            ranks[m++] = r;"),
     "bruteforce_thread_start_not_gray": ("uint64_t x = J->lo ^ (J->lo >> 1);", "uint64_t x = J->lo;"),
     "bruteforce_ranges_shifted": ("jobs[t].lo = total / nthreads * t + (t < (int)(total % nthreads) ? t : total % nthreads);",
                                   "jobs[t].lo = total / nthreads * t + (t < (int)(total % nthreads) ? t : total % nthreads) - (t > 0);"),

@@ -138,6 +138,8 @@ def check_gammas(rows, n, k):
         if r == k:
             S = order[:k]
             assert S == sorted(S) and not used.intersection(S)
+            # the reduction order: the set's columns ascending, then every other column ascending
+            assert order == S + [c for c in range(n) if c not in S]
             used.update(S)
             # identity on S_j, row i <-> i-th column of S_j
             for i in range(k):
@@ -148,7 +150,7 @@ def check_gammas(rows, n, k):
         else:
             assert j == len(orders) - 1            # only the last set may be partial
             rest = [c for c in range(n) if c not in used]
-            assert order[:len(rest)] == rest
+            assert order == rest + sorted(used)
             assert T.gf2_rank([T.column(rows, c) for c in rest]) == r
         # reduced echelon form under `order`: leading entries advance, pivot columns unit
         lead = []
@@ -183,6 +185,27 @@ def test_info_sets_systematic_first_set_is_identity():
     assert ranks == [64, 64]
     assert orders[0][:64] == list(range(64))
     assert orders[1][:64] == list(range(64, 128))
+
+
+def test_info_sets_leftover_rank_one_and_zero():
+    """Section 2.1's disjoint information sets, as read here: after the full sets, all the
+    leftover columns form the last set, of their own rank k_m, kept when k_m >= 1 and dropped
+    when k_m = 0.  G = [I_4 | I_4 | e_0] has two identity sets and one leftover column of rank
+    1; G = [I_4 | I_4 | 0] has an all-zero leftover column.  d = 2 for both (x = e_1 gives
+    (e_1, e_1, 0)), as the brute force finds."""
+    k, n = 4, 9
+    for last, want_ranks in ((1, [4, 4, 1]), (0, [4, 4])):
+        rows = [(1 << i) | (1 << (k + i)) | ((last << (2 * k)) if i == 0 else 0) for i in range(k)]
+        G = T.pack(rows, n)
+        orders, ranks = O.info_sets(G, n, k)
+        assert ranks == want_ranks
+        assert orders[0] == list(range(n)) and orders[1] == list(range(k, 2 * k)) + list(range(k)) + [2 * k]
+        if last:
+            assert orders[2] == [2 * k] + list(range(2 * k))
+        check_gammas(rows, n, k)
+        res = O.bz(G, n, k)
+        assert res.d == O.bruteforce(G, n, k)[0] == 2
+        assert res.m == len(want_ranks)
 
 
 def test_rank_errors():
