@@ -86,6 +86,27 @@ def test_gamma_bit_exact_with_oracle(B, n, k, seed):
         B.md_destroy(h)
 
 
+def test_gamma_leftover_sets_match_oracle(B):
+    """The library's information sets follow the oracle on codes built to have a leftover set
+    of rank 1 ([I_4 | I_4 | e_0]: three matrices, ranks 4, 4, 1) and an all-zero leftover
+    column ([I_4 | I_4 | 0]: two matrices): the same m, ranks, column orders and Gamma_j."""
+    k, n = 4, 9
+    for last, want in ((1, [4, 4, 1]), (0, [4, 4])):
+        rows = [(1 << i) | (1 << (k + i)) | ((last << (2 * k)) if i == 0 else 0) for i in range(k)]
+        G = T.pack(rows, n)
+        gams, ranks, orders = O.gammas(G, n, k)
+        assert ranks == want
+        h = B.md_create(G, n, k)
+        try:
+            info = B.md_info_get(h)
+            assert info["m"] == len(want) and info["ranks"] == want
+            for j in range(len(want)):
+                rj, oj = B.md_gamma(h, j, n, k)
+                assert np.array_equal(rj, gams[j]) and oj == orders[j], (last, j)
+        finally:
+            B.md_destroy(h)
+
+
 def test_gamma_textbook(B):
     for name, (ctor, d, _) in T.TEXTBOOK.items():
         rows, n, k = ctor()
