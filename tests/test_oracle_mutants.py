@@ -61,6 +61,15 @@ MUTANTS = {
                                        "            for (int col = n - 1; col >= 0; col--) if (!in_set[col]) order[pos++] = col;\n            ranks[m++] = k;"),
     "partial_set_order_rest_descending": ("            for (int col = 0; col < n; col++) if (!in_set[col]) order[pos++] = col;\n            ranks[m++] = r;",
                                           "            for (int col = n - 1; col >= 0; col--) if (!in_set[col]) order[pos++] = col;\n            ranks[m++] = r;"),
+    "gamma_pivot_search_from_row0": ("    for (int p = 0; p < n && r < k; p++) {\n        int col = order[p];\n        int s = -1;\n        for (int t = r; t < k; t++)",
+                                     "    for (int p = 0; p < n && r < k; p++) {\n        int col = order[p];\n        int s = -1;\n        for (int t = 0; t < k; t++)"),
+    "bz_skips_stage_k": ("for (int g = 1; g <= k && !stop; g++) {", "for (int g = 1; g < k && !stop; g++) {"),
+    "unrank_top_low": ("    int top = k - 1;\n    for (int i = g; i >= 1; i--) {\n        int v = top;",
+                       "    int top = k - 2;\n    for (int i = g; i >= 1; i--) {\n        int v = top;"),
+    "scan_range_not_clamped": ("    if (r1 > total) r1 = total;\n    if (r0 > r1) r0 = r1;\n    if (nthreads < 1) nthreads = 1;\n    if (nthreads > 256) nthreads = 256;\n    uint64_t span",
+                               "    if (r0 > r1) r0 = r1;\n    if (nthreads < 1) nthreads = 1;\n    if (nthreads > 256) nthreads = 256;\n    uint64_t span"),
+    "info_sets_skip_rank_check": ("    if (mdo_rank(G, n, k) != k) return MDO_ERANK;\n    int used", "    int used"),
+    "bz_starts_at_L0": ("    int64_t L = 1;\n", "    int64_t L = 0;\n"),
     "bruteforce_thread_start_not_gray": ("uint64_t x = J->lo ^ (J->lo >> 1);", "uint64_t x = J->lo;"),
     "bruteforce_ranges_shifted": ("jobs[t].lo = total / nthreads * t + (t < (int)(total % nthreads) ? t : total % nthreads);",
                                   "jobs[t].lo = total / nthreads * t + (t < (int)(total % nthreads) ? t : total % nthreads) - (t > 0);"),

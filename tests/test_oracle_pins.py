@@ -208,6 +208,19 @@ def test_info_sets_leftover_rank_one_and_zero():
         assert res.m == len(want_ranks)
 
 
+def test_bz_weight_one_codeword_stops_at_once():
+    """Alg. 1 starts from L = 1 (every nonzero codeword has weight >= 1), so a weight-1
+    codeword found in the first matrix at stage 1 ends the run before any other level:
+    rows 0001 and 1110 (n = 4, k = 2) have the full set {0, 1}, a leftover set {2, 3} of
+    rank 1, and d = 1 from row 0."""
+    rows = [0b0001, 0b1110]
+    G = T.pack(rows, 4)
+    res = O.bz(G, 4, 2)
+    assert res.d == 1 == O.bruteforce(G, 4, 2)[0]
+    assert res.m == 2
+    assert [lv[:2] for lv in res.levels] == [(1, 0)] and res.stop == (1, 0)
+
+
 def test_rank_errors():
     rows = T.random_rows(20, 6, 11)
     bad = T.pack(rows[:5] + [rows[0] ^ rows[1]], 20)
@@ -377,6 +390,22 @@ def test_scan_ranges_compose():
     best = min(parts)          # (w, rank) lexicographic; ranges are disjoint
     assert best == whole
     assert O.scan(gams[0], 60, 24, g, 5, 5) == (61, (1 << 64) - 1)
+
+
+def test_scan_range_past_the_level_is_clamped():
+    """A rank range reaching past the level's C(k, g) combinations covers the level's end and
+    no more: r1 beyond the end gives the same as r1 = C(k, g), and a range starting at or past
+    the end is empty (weight n + 1, no rank)."""
+    rows = T.random_rows(40, 12, 19)
+    G = T.pack(rows, 40)
+    gams, _, _ = O.gammas(G, 40, 12)
+    for g in (1, 3, 6):
+        total = math.comb(12, g)
+        for r0 in (0, total // 2, total - 1):
+            want = O.scan(gams[0], 40, 12, g, r0, total)
+            for threads in (1, 3):
+                assert O.scan(gams[0], 40, 12, g, r0, total + 5, threads=threads) == want
+        assert O.scan(gams[0], 40, 12, g, total, total + 7) == (41, (1 << 64) - 1)
 
 
 def test_scan_subranges_and_threads_against_enumeration():
