@@ -50,11 +50,16 @@ def test_create_validation(B):
     with pytest.raises(B.MDError) as e:
         B.md_create(T.pack(rows[:9] + [rows[0] ^ rows[1]], 40), 40, 10)
     assert e.value.code == B.MD_ERANK
-    bad = G.copy()
-    bad[0, 0] |= np.uint64(1 << 45)                      # a bit beyond column n-1
-    with pytest.raises(B.MDError) as e:
-        B.md_create(bad, 40, 10)
-    assert e.value.code == B.MD_EINVAL
+    # any padding bit set: the first one (column n), one further on, the last of the word,
+    # and a padding bit in the last word of a wider row (n = 130: columns 130..191)
+    for n_, k_, word, bit in ((40, 10, 0, 40), (40, 10, 0, 45), (40, 10, 0, 63), (130, 20, 2, 2), (130, 20, 2, 63)):
+        rows_ = T.random_rows(n_, k_, 2)
+        bad = T.pack(rows_, n_)
+        B.md_destroy(B.md_create(bad, n_, k_))               # valid without the bit
+        bad[k_ - 1, word] |= np.uint64(1 << bit)
+        with pytest.raises(B.MDError) as e:
+            B.md_create(bad, n_, k_)
+        assert e.value.code == B.MD_EINVAL, (n_, word, bit)
     big = np.zeros((1, 5), dtype=np.uint64)
     big[0, 0] = 1
     with pytest.raises(B.MDError) as e:
