@@ -24,6 +24,7 @@ tests) on bounded samples of the same workload, on this host's cores.
 from __future__ import annotations
 
 import argparse
+import atexit
 import json
 import math
 import os
@@ -126,8 +127,13 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
+            atexit.register(self._end)          # a leg that fails before stop() leaves none running
         except OSError:
             self.proc = None
+
+    def _end(self):
+        if self.proc and self.proc.poll() is None:
+            self.proc.kill()
 
     def _read(self):
         for line in self.proc.stdout:
@@ -424,9 +430,20 @@ def run_ours(args):
         # clock the timed region ran at: a second denominator beside the cuBLAS-derived peak
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         mhz = clocks.get("sm_mhz") or measured_peaks().get("sm_max_mhz") or NOMINAL_MAX_MHZ
-        roofline["clock_matched"] = clock_matched(roofline, B.md_mma_rate(), sms, mhz)
+        try:
+            roofline["clock_matched"] = clock_matched(roofline, B.md_mma_rate(), sms, mhz)
+        except B.MDError as e:                  # the headline line is printed either way
+            roofline["clock_matched"] = {"error": str(e)}
 
-    if rank == 0 and not args.no_e2e:
+    def leg(key, fn):
+        """A measurement after the timed steps: its failure is recorded under its key, and the
+        line (with the timed value) is printed all the same."""
+        try:
+            fn()
+        except Exception as e:                  # noqa: BLE001 -- reported in the JSON line
+            line[key] = {"error": "%s: %s" % (type(e).__name__, e)}
+
+    def e2e_leg():
         # end to end through the C ABI from host buffers: create (host G), compute, destroy
         opt_e = B.md_options_init(max_stage=args.max_stage, filter=args.filter, tensor=args.tensor)
         times, h2d, d2h, cwe = [], 0, 0, 0
@@ -444,14 +461,14 @@ def run_ours(args):
         line["e2e"] = {"value": cwe / sum(times), "unit": "codewords/s", "steps": e2e_steps,
                        "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps}
 
-    if rank == 0 and ws == 1 and not args.no_cpu:
+    def cpu_leg():
         threads = os.cpu_count() or 1
         rate, size, dt = oracle_sample_rate(G, n, k, args.max_stage, args.cpu_seconds, threads)
         line["cpu_baseline"] = {"value": rate, "unit": "codewords/s", "cores": threads, "kind": "oracle",
                                 "sample": "colex-rank prefix of level (g=%d, Gamma_1): %d combinations, %.1f s"
                                           % (args.max_stage, size, dt)}
 
-    if rank == 0 and ws == 1 and not args.no_time_to_d:
+    def time_to_d_leg():
         opt_f = B.md_options_init(filter=args.filter, tensor=args.tensor, stream=stream.cuda_stream)
         hf = B.md_create(G, n, k, opt_f)
         e0 = torch.cuda.Event(enable_timing=True)
@@ -468,7 +485,7 @@ def run_ours(args):
                              "codewords": inf["codewords"], "stop_stage": inf["stop_g"],
                              "complete": inf["complete"]}
 
-    if rank == 0 and ws == 1 and args.tensor and not args.no_popcount and args.workload == "rand200x100":
+    def popcount_leg():
         # the popcount kernels on the same workload (md_options.tensor = 0), against the POPC
         # peak measured on this GPU: its rate per SM and clock x SMs x the SM clock
         per_sm_clk = B.md_popc_rate()
@@ -493,7 +510,7 @@ def run_ours(args):
                    "clocks": clocks_p, "run": "md_compute with tensor = 0, stages g <= %d" % args.max_stage})
         line["roofline_popcount"] = rp
 
-    if rank == 0 and ws == 1 and not args.no_batch:
+    def batch_leg():
         import tempfile
         cache = os.path.join(tempfile.gettempdir(), "md_tune_bench_%d.json" % os.getpid())
         try:
@@ -503,8 +520,21 @@ def run_ours(args):
             if os.path.exists(cache):
                 os.remove(cache)
 
-    if rank == 0 and ws == 1 and not args.no_serve:
+    def serve_leg():
         line["serve"] = serve_measure(args, B, inputs)
+
+    if rank == 0 and not args.no_e2e:
+        leg("e2e", e2e_leg)
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        leg("cpu_baseline", cpu_leg)
+    if rank == 0 and ws == 1 and not args.no_time_to_d:
+        leg("time_to_d", time_to_d_leg)
+    if rank == 0 and ws == 1 and args.tensor and not args.no_popcount and args.workload == "rand200x100":
+        leg("roofline_popcount", popcount_leg)
+    if rank == 0 and ws == 1 and not args.no_batch:
+        leg("batch", batch_leg)
+    if rank == 0 and ws == 1 and not args.no_serve:
+        leg("serve", serve_leg)
 
     if args.verbose and rank == 0:
         for lv in lev_all[0]:
