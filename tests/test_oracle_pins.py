@@ -221,6 +221,22 @@ def test_bz_weight_one_codeword_stops_at_once():
     assert [lv[:2] for lv in res.levels] == [(1, 0)] and res.stop == (1, 0)
 
 
+def test_rand64x32_bz_equals_the_definition():
+    """At the [64,32] workload itself (seed 1), Alg. 1's d equals the definition's (Section
+    2.1): the least weight over all 2^32 - 1 nonzero messages, by the multithreaded brute
+    force, whose weight distribution covers all 2^32 codewords once.  The witness has that
+    weight and lies in the row space."""
+    from paper_1911_08963_gb300 import inputs
+    G, n, k = inputs.single_code("rand64x32")
+    d_bf, dist = O.bruteforce(G, n, k, threads=os.cpu_count() or 4)
+    assert int(dist.sum()) == 1 << k and int(dist[0]) == 1
+    res = O.bz(G, n, k)
+    assert res.d == d_bf
+    rows = T.unpack(G)
+    wv = T.unpack(res.witness.reshape(1, -1))[0]
+    assert T.wt(wv) == d_bf and T.solve_message(rows, wv) not in (None, 0)
+
+
 def test_rank_errors():
     rows = T.random_rows(20, 6, 11)
     bad = T.pack(rows[:5] + [rows[0] ^ rows[1]], 20)
